@@ -1,0 +1,164 @@
+/*
+ * peps.h -- C ABI of the GB300 PEPS sampling path (libpeps.so).
+ *
+ * The library evaluates, for a fixed finite open-boundary PEPS (Eq. 1 of
+ * Liu, Dong, Han, Guo, He, "Gradient optimization of finite projected
+ * entangled pair states", arXiv:1611.09467) and a batch of spin
+ * configurations S, the quantities of the Monte Carlo scheme of Sec. II:
+ *   - W(S) = psi(S), the single-layer network at fixed S (Fig. 1c),
+ *     contracted row by row with a boundary MPS of bond dimension Dc (Fig. 1d);
+ *   - E(S) = sum_S' W(S')/W(S) <S'|H|S> for the J1-J2 Heisenberg model of
+ *     Sec. IV (spin 1/2, S = sigma/2, open boundaries);
+ *   - Delta(S) = B(S)/W(S) = d ln psi / dA (Sec. II, B the environment of a site);
+ *   - the MC estimates of the energy and of dE/dA = 2<Delta E> - 2<Delta><E>;
+ *   - Metropolis sweeps that sample S with weight W^2.
+ *
+ * Conventions
+ *   - Lattice Ly rows x Lx columns, site i = row * Lx + col.  Spin s in {0,1},
+ *     s = 0 is S^z = +1/2.  A configuration is ceil(N/64) uint64 words,
+ *     bit i of word i/64 is s_i.
+ *   - Site tensors A[N][d=2][D][D][D][D] in the index order (l, r, u, d) of
+ *     Eq. 1, padded to D on open edges: entries past the true edge dimension
+ *     (one) must be zero.
+ *   - All array arguments named *_dev are device pointers owned by the caller
+ *     (the library never frees them); *_host are host pointers.  Work is
+ *     enqueued on the context's stream; calls return after enqueueing except
+ *     where noted.  Return values report argument, allocation and launch
+ *     errors only; per-configuration problems go to status_dev.
+ *   - Per-configuration status: 0 ok, PEPS_EINVAL (popcount != N/2),
+ *     PEPS_ENUMERIC (some W is exactly zero: ln|psi| = -inf, sign 0, E and
+ *     Delta undefined, excluded from the averages).
+ *   - A context is not thread-safe; use one context per stream.
+ *   - Readings of points the paper leaves open: zip-up truncation with SVD
+ *     cut to the Dc largest singular values, rows absorbed with alternating
+ *     direction; ratios and Delta use the environments of S and the W of the
+ *     same single-row (horizontal pairs, Delta) or two-row (vertical and
+ *     diagonal pairs) sandwich; next-nearest pairs are both diagonals of
+ *     each plaquette.
+ */
+#ifndef PEPS_H
+#define PEPS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct peps_ctx peps_ctx;
+
+typedef enum {
+  PEPS_OK = 0,
+  PEPS_EINVAL = 1,    /* invalid argument or configuration */
+  PEPS_ENOMEM = 2,    /* device allocation failed */
+  PEPS_ECUDA = 3,     /* CUDA runtime or launch error */
+  PEPS_ETIMEOUT = 4,  /* a bounded device wait gave up */
+  PEPS_ENUMERIC = 5   /* zero amplitude */
+} peps_status;
+
+typedef enum {
+  PEPS_FP64 = 0,        /* contractions and truncation in FP64 */
+  PEPS_FP32 = 1,        /* contractions and truncation in FP32; log scales and reductions FP64 */
+  PEPS_MIXED_TF32 = 2,  /* reserved: tensor-core absorptions */
+  PEPS_MIXED_BF16 = 3   /* reserved: tensor-core absorptions */
+} peps_precision;
+
+typedef struct {
+  int Lx, Ly;          /* columns, rows; 2 <= Lx, Ly <= 64, N = Lx * Ly <= 4096 */
+  int d;               /* local dimension, must be 2 */
+  int D;               /* virtual bond dimension, 1 <= D <= 16 */
+  int Dc;              /* boundary-MPS cut-off, 1 <= Dc <= 32, Dc * D <= 256 */
+  double J1, J2;       /* nearest / next-nearest couplings (Sec. IV) */
+  int prec;            /* peps_precision */
+  double workspace_gb; /* device workspace budget for environments; 0 -> 24 GB */
+} peps_params;
+
+/* Creates a context: validates the parameters, copies A_host
+ * ([N][2][D^4] FP64, padded as above) to the device in the context's
+ * precision.  cuda_stream is a cudaStream_t (NULL = legacy default stream).
+ * Fig. 1c / Eq. 1. */
+peps_status peps_create(const peps_params* params, const double* A_host, void* cuda_stream, peps_ctx** out);
+
+/* Frees the context and its device memory. */
+peps_status peps_destroy(peps_ctx* ctx);
+
+/* Replaces the site tensors (same shapes).  Eq. 1. */
+peps_status peps_set_tensors(peps_ctx* ctx, const double* A_host);
+
+/* ln|psi(S)| and sign psi(S) from the top-down boundary-MPS sweep (Fig. 1d).
+ * S_dev [n][ceil(N/64)]; logabs_dev [n] FP64; sign_dev [n] int8 (+1, -1, 0);
+ * status_dev [n] int32 or NULL. */
+peps_status peps_amplitudes(peps_ctx* ctx, const uint64_t* S_dev, int n, double* logabs_dev, int8_t* sign_dev,
+                            int32_t* status_dev);
+
+/* E(S) per configuration (Sec. II local energy, Sec. IV Hamiltonian).
+ * eloc_dev [n] FP64; status_dev [n] or NULL. */
+peps_status peps_local_energy(peps_ctx* ctx, const uint64_t* S_dev, int n, double* eloc_dev, int32_t* status_dev);
+
+/* Delta(S) = B/W (Sec. II) for the spin block selected by each s_i:
+ * O_dev [n][N][D^4] in the context's precision (double for PEPS_FP64,
+ * float otherwise), index order (l, r, u, d), zero at padded entries. */
+peps_status peps_log_derivatives(peps_ctx* ctx, const uint64_t* S_dev, int n, void* O_dev);
+
+/* All per-configuration outputs in one pass; any output may be NULL (work
+ * not needed for the requested outputs is skipped). */
+peps_status peps_evaluate(peps_ctx* ctx, const uint64_t* S_dev, int n, double* logabs_dev, int8_t* sign_dev,
+                          double* eloc_dev, void* O_dev, int32_t* status_dev);
+
+/* MC estimates over the n given configurations (plain sample means; the
+ * configurations are taken as samples of W^2, Sec. II):
+ *   energy per site <E>/N -> *energy_per_site_host (this call synchronises
+ *   the stream), grad_dev [N][2][D^4] FP64 = 2(<Delta E> - <Delta><E>),
+ *   cov_dev (optional) = grad / 2.  Optional per-configuration outputs
+ *   logabs_dev, sign_dev, eloc_dev, status_dev may be NULL.  Configurations
+ *   with a non-zero status are left out of the means.
+ *   *n_used_host (optional) receives the number of configurations used. */
+peps_status peps_gradient(peps_ctx* ctx, const uint64_t* S_dev, int n, double* energy_per_site_host, double* grad_dev,
+                          double* cov_dev, double* logabs_dev, int8_t* sign_dev, double* eloc_dev,
+                          int32_t* status_dev, int* n_used_host);
+
+/* nsweeps Metropolis sweeps per configuration (chain), in place on S_dev.
+ * A sweep visits the nearest-neighbour bonds in the order: horizontal
+ * row-major, then vertical row-major; an antiparallel pair is exchanged with
+ * probability min(1, (W(S')/W(S))^2) (sampling with weight W^2, Sec. II),
+ * with W(S')/W(S) computed from the environments of the current S as in
+ * peps_local_energy.  The uniform draw for (chain, sweep, bond) is
+ * u = (h >> 11) * 2^-53 with h = SplitMix64 keyed by (seed, chain0 + index,
+ * sweep0 + k, bond index); accepted_dev [n] int64 (optional) is incremented
+ * by the number of accepted exchanges. */
+peps_status peps_mc_sweep(peps_ctx* ctx, uint64_t* S_dev, int n, int nsweeps, uint64_t seed, uint64_t chain0,
+                          uint64_t sweep0, int64_t* accepted_dev);
+
+/* Waits for the context's stream. */
+peps_status peps_synchronize(peps_ctx* ctx);
+
+/* Human-readable name of a status code. */
+const char* peps_status_str(peps_status s);
+
+/* Last error message of the calling thread (empty if none). */
+const char* peps_last_error(void);
+
+/* Host-only check of the contraction programs, no GPU involved: runs the
+ * same index descriptors the kernels use on host FP64 buffers.
+ *   op 0 single-row left transfer   in: F, Mu, T, Md        out: F'
+ *   op 1 single-row right transfer  in: G, Mu, T, Md        out: G'
+ *   op 2 site environment B         in: F, Mu, Md, G        out: B
+ *   op 3 two-row left transfer      in: E, Mu, T1, T2, Md   out: E'
+ *   op 4 two-row right transfer     in: H, Mu, T1, T2, Md   out: H'
+ * Tensors are padded as documented in contract.cuh. */
+peps_status peps_debug_host_op(int op, int D, int Dc, const double* in0, const double* in1, const double* in2,
+                               const double* in3, const double* in4, double* out);
+
+/* Host-only check of one zip-up column (Fig. 1d): dims = {k, a, b, i, l, r, o,
+ * sl, sr, si, so}; lr = 1 left-to-right (carry C [k][a][l], output X
+ * [(k,o)][(b,r)]), lr = 0 right-to-left (carry C [b][r][k], output X
+ * [(o,k)][(a,l)]).  M padded [Dc][D][Dc], T padded D^4 read with strides. */
+peps_status peps_debug_host_zip(int lr, int D, int Dc, const int* dims, const double* C, const double* M,
+                                const double* T, double* X);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PEPS_H */

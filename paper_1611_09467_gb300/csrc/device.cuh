@@ -1,0 +1,567 @@
+// Device building blocks: CTA-wide strided GEMM, reductions, contraction
+// programs, and the truncation of the boundary MPS (dominant left singular
+// subspace of a small dense matrix).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "contract.cuh"
+
+namespace peps {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+
+template <typename R> struct Eps;
+template <> struct Eps<double> {
+  static constexpr double eps = 2.220446049250313e-16;
+  static constexpr double tiny = 2.2250738585072014e-308;
+  static constexpr int bits = 53;
+};
+template <> struct Eps<float> {
+  static constexpr float eps = 1.1920929e-07f;
+  static constexpr float tiny = 1.17549435e-38f;
+  static constexpr int bits = 24;
+};
+
+__device__ __forceinline__ double dsqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float dsqrt(float x) { return sqrtf(x); }
+
+template <typename R>
+__device__ __forceinline__ R warp_sum(R v, int width = 32) {
+  for (int o = width / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, width);
+  return v;
+}
+template <typename R>
+__device__ __forceinline__ R warp_max(R v) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Block-wide sum; `red` is shared scratch of >= kWarps elements.  All threads
+// get the result.  Contains two barriers.
+template <typename R>
+__device__ R block_sum(R v, R* red) {
+  v = warp_sum(v);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  R s = 0;
+  for (int i = 0; i < kWarps; ++i) s += red[i];
+  __syncthreads();
+  return s;
+}
+
+// ------------------------------------------------------------- CTA GEMM
+// Each thread owns 4x4 output tiles; operands are read through the index
+// maps of the descriptor (see contract.cuh).  No barrier inside: callers
+// synchronise between dependent steps.
+template <typename R>
+__device__ void cta_gemm(const GemmDesc& g, const R* __restrict__ A, const R* __restrict__ B,
+                         R* __restrict__ C, bool accumulate) {
+  const int tm = (g.M + 3) >> 2, tn = (g.N + 3) >> 2;
+  const int per_batch = tm * tn;
+  const int total = per_batch * g.nb;
+  const int kn2 = g.ak.n2;
+  const int k1n = g.K / kn2;
+  for (int t = threadIdx.x; t < total; t += blockDim.x) {
+    const int bt = t / per_batch, tt = t - bt * per_batch;
+    const int i0 = (tt / tn) * 4, j0 = (tt % tn) * 4;
+    const R* Ab = A + (size_t)bt * g.sa;
+    const R* Bb = B + (size_t)bt * g.sb;
+    R* Cb = C + (size_t)bt * g.sc;
+    int ao[4], cm[4], bo[4], cn[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int i = min(i0 + q, g.M - 1), j = min(j0 + q, g.N - 1);
+      ao[q] = ixoff(g.am, i);
+      cm[q] = ixoff(g.cm, i);
+      bo[q] = ixoff(g.bn, j);
+      cn[q] = ixoff(g.cn, j);
+    }
+    R acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[a][b] = R(0);
+    for (int k1 = 0; k1 < k1n; ++k1) {
+      const R* pa = Ab + k1 * g.ak.s1;
+      const R* pb = Bb + k1 * g.bk.s1;
+      for (int k2 = 0; k2 < kn2; ++k2) {
+        R av[4], bv[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          av[q] = pa[ao[q] + k2 * g.ak.s2];
+          bv[q] = pb[bo[q] + k2 * g.bk.s2];
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      if (i0 + a >= g.M) break;
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        if (j0 + b >= g.N) break;
+        R* p = Cb + cm[a] + cn[b];
+        *p = accumulate ? *p + acc[a][b] : acc[a][b];
+      }
+    }
+  }
+}
+
+// ------------------------------------------------- contraction programs
+enum OpId { OP_COL1_LEFT = 0, OP_COL1_RIGHT = 1, OP_SITE_ENV = 2, OP_COL2_LEFT = 3, OP_COL2_RIGHT = 4 };
+enum BufId { IN0 = 0, IN1, IN2, IN3, IN4, TMP0, TMP1, OUT };
+struct Step {
+  int s, a, b, c;
+};
+
+PEPS_HD int op_nsteps(int op) { return (op == OP_COL2_LEFT || op == OP_COL2_RIGHT) ? 4 : 3; }
+
+// Which buffers each step reads and writes.  Inputs per op:
+//   COL1_LEFT : IN0 = F_{c-1}, IN1 = Mu, IN2 = T, IN3 = Md        -> F_c
+//   COL1_RIGHT: IN0 = G_{c+1}, IN1 = Mu, IN2 = T, IN3 = Md        -> G_c
+//   SITE_ENV  : IN0 = F_{c-1}, IN1 = Mu, IN2 = Md, IN3 = G_{c+1}  -> B_c
+//   COL2_LEFT : IN0 = E_{c-1}, IN1 = Mu, IN2 = T1, IN3 = T2, IN4 = Md -> E_c
+//   COL2_RIGHT: IN0 = H_{c+1}, IN1 = Mu, IN2 = T1, IN3 = T2, IN4 = Md -> H_c
+PEPS_HD Step op_step_bufs(int op, int s) {
+  switch (op) {
+    case OP_COL1_LEFT:
+      return s == 0 ? Step{0, IN0, IN1, TMP0} : s == 1 ? Step{1, TMP0, IN2, TMP1} : Step{2, TMP1, IN3, OUT};
+    case OP_COL1_RIGHT:
+      return s == 0 ? Step{0, IN1, IN0, TMP0} : s == 1 ? Step{1, TMP0, IN2, TMP1} : Step{2, TMP1, IN3, OUT};
+    case OP_SITE_ENV:
+      return s == 0 ? Step{0, IN2, IN3, TMP0} : s == 1 ? Step{1, IN1, TMP0, TMP1} : Step{2, IN0, TMP1, OUT};
+    case OP_COL2_LEFT:
+      return s == 0 ? Step{0, IN0, IN1, TMP0}
+           : s == 1 ? Step{1, TMP0, IN2, TMP1}
+           : s == 2 ? Step{2, TMP1, IN3, TMP0}
+                    : Step{3, TMP0, IN4, OUT};
+    default:
+      return s == 0 ? Step{0, IN1, IN0, TMP0}
+           : s == 1 ? Step{1, TMP0, IN2, TMP1}
+           : s == 2 ? Step{2, TMP1, IN3, TMP0}
+                    : Step{3, TMP0, IN4, OUT};
+  }
+}
+
+PEPS_HD GemmDesc op_desc(int op, int s, int D, int Dc) {
+  switch (op) {
+    case OP_COL1_LEFT: return col1_left_step(s, D, Dc);
+    case OP_COL1_RIGHT: return col1_right_step(s, D, Dc);
+    case OP_SITE_ENV: return site_env_step(s, D, Dc);
+    case OP_COL2_LEFT: return col2_left_step(s, D, Dc);
+    default: return col2_right_step(s, D, Dc);
+  }
+}
+
+// Runs one contraction program with the whole CTA; ends with a barrier.
+template <typename R>
+__device__ void run_op(int op, int D, int Dc, const R* in0, const R* in1, const R* in2, const R* in3,
+                       const R* in4, R* out, R* t0, R* t1) {
+  const int ns = op_nsteps(op);
+  for (int s = 0; s < ns; ++s) {
+    const Step st = op_step_bufs(op, s);
+    const GemmDesc g = op_desc(op, st.s, D, Dc);
+    const R* bufs[8] = {in0, in1, in2, in3, in4, t0, t1, out};
+    cta_gemm<R>(g, bufs[st.a], bufs[st.b], const_cast<R*>(bufs[st.c]), false);
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------ truncation
+// Dominant-K left singular subspace of a dense m x n matrix X (row-major),
+// used for the boundary-MPS cut-off (Fig. 1d, Dc).  Route: Householder
+// bidiagonalisation (Golub & Kahan 1965), the K largest singular values by
+// Sturm-count bisection on the Golub-Kahan tridiagonal form
+// [[0, B], [B^T, 0]] (perfect-shuffle ordering), singular vectors by inverse
+// iteration on that form, classical Gram-Schmidt with re-orthogonalisation,
+// and back-transformation by the stored reflectors.  Only the subspace
+// matters downstream (the kept projector is unique when sigma_K > sigma_K+1),
+// so any orthonormal basis of it is a valid result.
+template <typename R>
+struct TruncWork {
+  R* Wm;      // P x ldw
+  int ldw;
+  R* tau;     // 2 * Qmax (left reflectors, then right reflectors)
+  R* t;       // 2 * Qmax off-diagonal of the Golub-Kahan form
+  R* t2;      // squares of t
+  R* lam;     // Kmax
+  R* Z;       // Kmax x 2Qmax
+  R* lu;      // Kmax x 6 x 2Qmax
+  R* Ub;      // Qmax x Kmax
+  R* Uk;      // Pmax x Kmax
+  R* red;     // >= 64 (shared)
+  int Qmax;
+};
+
+// Element counts of the truncation workspace for P, Q <= pq and K <= kmax.
+PEPS_HD size_t trunc_ws_elems(int pq, int kmax, bool with_wm) {
+  size_t e = 0;
+  if (with_wm) e += (size_t)pq * (pq + 1);
+  e += 2 * (size_t)pq * 3;                // tau, t, t2
+  e += kmax;                              // lam
+  e += (size_t)kmax * 2 * pq;             // Z
+  e += (size_t)kmax * 6 * 2 * pq;         // lu
+  e += (size_t)pq * kmax * 2;             // Ub, Uk
+  return e + 64;
+}
+
+// Householder vector for x = (alpha, rest): returns tau, scale for rest, beta.
+template <typename R>
+__device__ __forceinline__ void householder(R alpha, R ss, R& tau, R& scale, R& beta) {
+  if (ss <= R(0)) {
+    tau = R(0);
+    scale = R(0);
+    beta = alpha;
+  } else {
+    const R nrm = dsqrt(alpha * alpha + ss);
+    beta = alpha >= R(0) ? -nrm : nrm;
+    tau = (beta - alpha) / beta;
+    scale = R(1) / (alpha - beta);
+  }
+}
+
+template <typename R>
+__device__ int sturm_count(const R* t2, int n2, R x, R pivmin) {
+  int cnt = 0;
+  R q = -x;
+  if (fabs(q) < pivmin) q = -pivmin;
+  if (q < R(0)) ++cnt;
+  for (int i = 1; i < n2; ++i) {
+    q = -x - t2[i - 1] / q;
+    if (fabs(q) < pivmin) q = -pivmin;
+    if (q < R(0)) ++cnt;
+  }
+  return cnt;
+}
+
+// Inverse iteration for one eigenvalue of the n2 x n2 zero-diagonal
+// symmetric tridiagonal with off-diagonal t: Gaussian elimination with
+// partial pivoting on (T - lam I), three solves from a fixed pseudo-random
+// start vector.  Sequential, one thread.
+template <typename R>
+__device__ void inverse_iteration(const R* t, int n2, R lam, R pivtiny, R* ws, R* z, unsigned seed) {
+  R* dd = ws;
+  R* du = ws + n2;
+  R* du2 = ws + 2 * n2;
+  R* mult = ws + 3 * n2;
+  R* piv = ws + 4 * n2;
+  R* b = ws + 5 * n2;
+  for (int i = 0; i < n2; ++i) {
+    dd[i] = -lam;
+    du[i] = i < n2 - 1 ? t[i] : R(0);
+    du2[i] = R(0);
+  }
+  for (int i = 0; i < n2 - 1; ++i) {
+    const R sub = t[i];
+    R a = dd[i];
+    if (fabs(a) >= fabs(sub)) {
+      if (a == R(0)) a = dd[i] = pivtiny;
+      const R l = sub / a;
+      mult[i] = l;
+      piv[i] = R(0);
+      dd[i + 1] -= l * du[i];
+    } else {
+      const R l = a / sub;
+      mult[i] = l;
+      piv[i] = R(1);
+      dd[i] = sub;
+      const R tmp = du[i];
+      du[i] = dd[i + 1];
+      dd[i + 1] = tmp - l * dd[i + 1];
+      if (i < n2 - 2) {
+        du2[i] = du[i + 1];
+        du[i + 1] = -l * du[i + 1];
+      }
+    }
+  }
+  for (int i = 0; i < n2; ++i)
+    if (fabs(dd[i]) < pivtiny) dd[i] = dd[i] < R(0) ? -pivtiny : pivtiny;
+  // start vector
+  unsigned h = seed * 2654435761u + 12345u;
+  for (int i = 0; i < n2; ++i) {
+    h ^= h << 13; h ^= h >> 17; h ^= h << 5;
+    b[i] = R((int)(h & 0xffffu) - 32768) / R(32768) + R(0.001);
+  }
+  for (int it = 0; it < 3; ++it) {
+    for (int i = 0; i < n2 - 1; ++i) {
+      if (piv[i] == R(0)) {
+        b[i + 1] -= mult[i] * b[i];
+      } else {
+        const R tmp = b[i];
+        b[i] = b[i + 1];
+        b[i + 1] = tmp - mult[i] * b[i];
+      }
+    }
+    b[n2 - 1] /= dd[n2 - 1];
+    if (n2 >= 2) b[n2 - 2] = (b[n2 - 2] - du[n2 - 2] * b[n2 - 1]) / dd[n2 - 2];
+    for (int i = n2 - 3; i >= 0; --i) b[i] = (b[i] - du[i] * b[i + 1] - du2[i] * b[i + 2]) / dd[i];
+    R mx = R(0);
+    for (int i = 0; i < n2; ++i) mx = fmax(mx, fabs(b[i]));
+    if (!(mx > R(0))) mx = R(1);
+    R ss = R(0);
+    for (int i = 0; i < n2; ++i) {
+      b[i] /= mx;
+      ss += b[i] * b[i];
+    }
+    const R inv = R(1) / dsqrt(ss);
+    for (int i = 0; i < n2; ++i) b[i] *= inv;
+  }
+  for (int i = 0; i < n2; ++i) z[i] = b[i];
+}
+
+// Writes U_K (m x K) through (uo_r, uo_c) and C' = U_K^T X (K x n) through
+// (co_r, co_c).  X is not modified.  K <= min(m, n), K <= 32.
+template <typename R>
+__device__ void cta_topk_left(const R* X, int m, int n, int K, TruncWork<R>& w, R* Uout, Ix uo_r,
+                              Ix uo_c, R* Cout, Ix co_r, Ix co_c) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (K == m) {
+    // Nothing is cut: any orthonormal basis of R^m works; take the identity.
+    for (int e = tid; e < m * m; e += blockDim.x) {
+      const int i = e / m, k = e % m;
+      Uout[ixoff(uo_r, i) + ixoff(uo_c, k)] = i == k ? R(1) : R(0);
+    }
+    for (int e = tid; e < m * n; e += blockDim.x) {
+      const int k = e / n, j = e % n;
+      Cout[ixoff(co_r, k) + ixoff(co_c, j)] = X[e];
+    }
+    __syncthreads();
+    return;
+  }
+  const bool tall = m >= n;
+  const int P = tall ? m : n, Q = tall ? n : m;
+  const int ld = w.ldw;
+  R* W = w.Wm;
+  for (int e = tid; e < m * n; e += blockDim.x) {
+    const int i = e / n, j = e % n;
+    if (tall) W[i * ld + j] = X[e];
+    else W[j * ld + i] = X[e];
+  }
+  __syncthreads();
+  R* tauL = w.tau;
+  R* tauR = w.tau + w.Qmax;
+  R* red = w.red;
+  // ---------------- bidiagonalisation: W = Q_L B Q_R^T, B upper bidiagonal
+  for (int j = 0; j < Q; ++j) {
+    if (warp == 0) {
+      R ss = R(0);
+      for (int i = j + 1 + lane; i < P; i += 32) {
+        const R v = W[i * ld + j];
+        ss += v * v;
+      }
+      ss = warp_sum(ss);
+      if (lane == 0) {
+        R tau, scale, beta;
+        householder(W[j * ld + j], ss, tau, scale, beta);
+        red[0] = tau;
+        red[1] = scale;
+        w.t[2 * j] = beta;
+        tauL[j] = tau;
+      }
+    }
+    __syncthreads();
+    {
+      const R tau = red[0], scale = red[1];
+      for (int i = j + 1 + tid; i < P; i += blockDim.x) W[i * ld + j] *= scale;
+      __syncthreads();
+      if (tau != R(0)) {
+        for (int c = j + 1 + warp; c < Q; c += kWarps) {
+          R s = lane == 0 ? W[j * ld + c] : R(0);
+          for (int i = j + 1 + lane; i < P; i += 32) s += W[i * ld + j] * W[i * ld + c];
+          s = warp_sum(s) * tau;
+          if (lane == 0) W[j * ld + c] -= s;
+          for (int i = j + 1 + lane; i < P; i += 32) W[i * ld + c] -= s * W[i * ld + j];
+        }
+      }
+      __syncthreads();
+    }
+    if (j < Q - 1) {
+      if (warp == 0) {
+        R ss = R(0);
+        for (int c = j + 2 + lane; c < Q; c += 32) {
+          const R v = W[j * ld + c];
+          ss += v * v;
+        }
+        ss = warp_sum(ss);
+        if (lane == 0) {
+          R tau, scale, beta;
+          householder(W[j * ld + j + 1], ss, tau, scale, beta);
+          red[2] = tau;
+          red[3] = scale;
+          w.t[2 * j + 1] = beta;
+          tauR[j] = tau;
+        }
+      }
+      __syncthreads();
+      const R tau = red[2], scale = red[3];
+      for (int c = j + 2 + tid; c < Q; c += blockDim.x) W[j * ld + c] *= scale;
+      __syncthreads();
+      if (tau != R(0)) {
+        for (int i = j + 1 + warp; i < P; i += kWarps) {
+          R s = lane == 0 ? W[i * ld + j + 1] : R(0);
+          for (int c = j + 2 + lane; c < Q; c += 32) s += W[i * ld + c] * W[j * ld + c];
+          s = warp_sum(s) * tau;
+          if (lane == 0) W[i * ld + j + 1] -= s;
+          for (int c = j + 2 + lane; c < Q; c += 32) W[i * ld + c] -= s * W[j * ld + c];
+        }
+      }
+      __syncthreads();
+    }
+  }
+  // ---------------- Sturm bisection for the K largest singular values
+  const int n2 = 2 * Q;
+  R tmax = R(0);
+  for (int i = tid; i < n2 - 1; i += blockDim.x) {
+    const R v = w.t[i];
+    w.t2[i] = v * v;
+    tmax = fmax(tmax, fabs(v));
+  }
+  tmax = warp_max(tmax);
+  if (lane == 0) red[8 + warp] = tmax;
+  __syncthreads();
+  tmax = R(0);
+  for (int i = 0; i < kWarps; ++i) tmax = fmax(tmax, red[8 + i]);
+  __syncthreads();
+  const R bound = R(2) * tmax * (R(1) + R(4) * Eps<R>::eps) + Eps<R>::tiny;
+  const R pivmin = Eps<R>::tiny * R(1024) * fmax(R(1), tmax * tmax);
+  {
+    const int G = K <= 16 ? 16 : 8;
+    const int gid = tid / G, gl = tid % G;
+    const int gbase = (lane / G) * G;
+    const double lg = log((double)(G + 1));
+    const int nit = (int)((Eps<R>::bits + 2) * 0.6931471805599453 / lg) + 2;
+    const int idx = n2 - 1 - gid;  // ascending index of the (gid+1)-th largest eigenvalue
+    R lo = R(0), hi = bound;
+    for (int it = 0; it < nit; ++it) {
+      const R step = (hi - lo) / R(G + 1);
+      bool pred = true;
+      if (gid < K) {
+        const R x = lo + step * R(gl + 1);
+        pred = sturm_count(w.t2, n2, x, pivmin) <= idx;
+      }
+      const unsigned bal = __ballot_sync(0xffffffffu, pred);
+      const unsigned bits = (bal >> gbase) & ((G == 32) ? 0xffffffffu : ((1u << G) - 1u));
+      const int gstar = __popc(bits) - 1;
+      const R nlo = gstar >= 0 ? lo + step * R(gstar + 1) : lo;
+      const R nhi = gstar + 1 < G ? lo + step * R(gstar + 2) : hi;
+      lo = nlo;
+      hi = nhi;
+    }
+    if (gid < K && gl == 0) w.lam[gid] = R(0.5) * (lo + hi);
+  }
+  __syncthreads();
+  // ---------------- inverse iteration, one thread per vector
+  const R pivtiny = Eps<R>::eps * fmax(tmax, Eps<R>::tiny * R(1e10));
+  if (tid < K)
+    inverse_iteration(w.t, n2, w.lam[tid], pivtiny, w.lu + (size_t)tid * 6 * n2, w.Z + (size_t)tid * n2,
+                      (unsigned)(tid + 1));
+  __syncthreads();
+  // extract u-parts (odd positions) for a tall matrix, v-parts (even) for a wide one
+  R* Ub = w.Ub;
+  for (int e = tid; e < Q * K; e += blockDim.x) {
+    const int i = e / K, k = e % K;
+    Ub[e] = w.Z[(size_t)k * n2 + 2 * i + (tall ? 1 : 0)];
+  }
+  __syncthreads();
+  // ---------------- Gram-Schmidt with re-orthogonalisation (CGS2)
+  for (int j = 0; j < K; ++j) {
+    for (int attempt = 0; attempt <= Q; ++attempt) {
+      R s = R(0);
+      for (int i = tid; i < Q; i += blockDim.x) s += Ub[i * K + j] * Ub[i * K + j];
+      R nrm0 = dsqrt(block_sum(s, red + 16));
+      if (nrm0 > R(0)) {
+        for (int i = tid; i < Q; i += blockDim.x) Ub[i * K + j] /= nrm0;
+        __syncthreads();
+      }
+      for (int pass = 0; pass < 2; ++pass) {
+        for (int p = warp; p < j; p += kWarps) {
+          R d = R(0);
+          for (int i = lane; i < Q; i += 32) d += Ub[i * K + p] * Ub[i * K + j];
+          d = warp_sum(d);
+          if (lane == 0) red[32 + p] = d;
+        }
+        __syncthreads();
+        for (int i = tid; i < Q; i += blockDim.x) {
+          R v = Ub[i * K + j];
+          for (int p = 0; p < j; ++p) v -= red[32 + p] * Ub[i * K + p];
+          Ub[i * K + j] = v;
+        }
+        __syncthreads();
+      }
+      s = R(0);
+      for (int i = tid; i < Q; i += blockDim.x) s += Ub[i * K + j] * Ub[i * K + j];
+      const R nrm = dsqrt(block_sum(s, red + 16));
+      if (nrm0 > R(0) && nrm > R(1e-3)) {
+        for (int i = tid; i < Q; i += blockDim.x) Ub[i * K + j] /= nrm;
+        __syncthreads();
+        break;
+      }
+      // degenerate direction (zero singular value or lost vector): try a unit vector
+      const int q = (j + attempt) % Q;
+      for (int i = tid; i < Q; i += blockDim.x) Ub[i * K + j] = i == q ? R(1) : R(0);
+      __syncthreads();
+    }
+  }
+  // ---------------- back-transformation, one thread group per column
+  R* Uk = w.Uk;
+  const int rowsU = tall ? P : Q;
+  for (int e = tid; e < rowsU * K; e += blockDim.x) {
+    const int i = e / K, k = e % K;
+    Uk[e] = i < Q ? Ub[i * K + k] : R(0);
+  }
+  __syncthreads();
+  {
+    // Every group runs the same loop (the shuffles need whole warps); groups
+    // beyond K compute on column 0 and discard the result.
+    const int G = K <= 8 ? 32 : (K <= 16 ? 16 : 8);
+    const int col = tid / G, gl = tid % G;
+    const bool act = col < K;
+    const int cc = act ? col : 0;
+    if (tall) {
+      for (int j = Q - 1; j >= 0; --j) {
+        const R tau = tauL[j];
+        if (tau == R(0)) continue;
+        R s = gl == 0 ? Uk[j * K + cc] : R(0);
+        for (int i = j + 1 + gl; i < P; i += G) s += W[i * ld + j] * Uk[i * K + cc];
+        s = warp_sum(s, G) * tau;
+        if (act) {
+          if (gl == 0) Uk[j * K + cc] -= s;
+          for (int i = j + 1 + gl; i < P; i += G) Uk[i * K + cc] -= s * W[i * ld + j];
+        }
+        __syncwarp();
+      }
+    } else {
+      for (int j = Q - 2; j >= 0; --j) {
+        const R tau = tauR[j];
+        if (tau == R(0)) continue;
+        R s = gl == 0 ? Uk[(j + 1) * K + cc] : R(0);
+        for (int c = j + 2 + gl; c < Q; c += G) s += W[j * ld + c] * Uk[c * K + cc];
+        s = warp_sum(s, G) * tau;
+        if (act) {
+          if (gl == 0) Uk[(j + 1) * K + cc] -= s;
+          for (int c = j + 2 + gl; c < Q; c += G) Uk[c * K + cc] -= s * W[j * ld + c];
+        }
+        __syncwarp();
+      }
+    }
+  }
+  __syncthreads();
+  // ---------------- outputs
+  for (int e = tid; e < m * K; e += blockDim.x) {
+    const int i = e / K, k = e % K;
+    Uout[ixoff(uo_r, i) + ixoff(uo_c, k)] = Uk[e];
+  }
+  // C' = U_K^T X
+  GemmDesc g = gemm(K, n, m, ix1(1), kx(m, 0, K), kx(m, 0, n), ix1(1), co_r, co_c);
+  cta_gemm<R>(g, Uk, X, Cout, false);
+  __syncthreads();
+}
+
+}  // namespace peps

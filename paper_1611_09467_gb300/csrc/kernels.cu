@@ -1,0 +1,796 @@
+// CUDA kernels of the PEPS sampling path (sm_103a).
+//
+//   k_boundary : boundary-MPS sweeps (Fig. 1d): top-down U_r (gives ln|psi|,
+//                sign) and bottom-up L_r, alternating zip-up with truncation
+//                to Dc.  One CTA per (configuration, sweep direction).
+//   k_row      : single-row sandwiches <U_{r-1}| row r |L_{r+1}>: W_r,
+//                amplitude ratios of horizontal spin exchanges, Delta = B/W
+//                (Sec. II).  One CTA per (configuration, row).
+//   k_pair     : two-row sandwiches <U_{r-1}| rows r,r+1 |L_{r+2}>: ratios
+//                of vertical and diagonal exchanges.  One CTA per
+//                (configuration, row pair).
+//   k_finalize : E(S) = diagonal + sum of (J/2) ratios (Sec. II with the
+//                Hamiltonian of Sec. IV), status.
+//   k_grad_*   : sums of O and E*O over configurations for
+//                dE/dA = 2<Delta E> - 2<Delta><E> (Sec. II).
+//   k_mc       : Metropolis sweeps over nearest-neighbour spin exchanges.
+//
+// Kernels are persistent over work items (grid-stride), so the per-CTA
+// scratch slots bound the workspace.
+#include <cstdio>
+
+#include "device.cuh"
+#include "kernels.h"
+
+namespace peps {
+
+__device__ __forceinline__ int spin_of(const uint64_t* sp, int i) { return (int)((sp[i >> 6] >> (i & 63)) & 1ull); }
+
+template <typename R>
+__device__ __forceinline__ const R* tptr(const KArgs<R>& a, int site, int s) {
+  const size_t D4 = (size_t)a.g.D * a.g.D * a.g.D * a.g.D;
+  return a.A + ((size_t)site * 2 + s) * D4;
+}
+
+struct TDims {
+  int l, r, u, d;
+};
+__device__ __forceinline__ TDims tdims(const Geometry& g, int row, int col) {
+  TDims t;
+  t.l = col == 0 ? 1 : g.D;
+  t.r = col == g.Lx - 1 ? 1 : g.D;
+  t.u = row == 0 ? 1 : g.D;
+  t.d = row == g.Ly - 1 ? 1 : g.D;
+  return t;
+}
+
+// ---------------------------------------------------------------- layouts
+size_t wm_smem_bytes(const Geometry& g, size_t elem) {
+  const size_t P = (size_t)g.Dc * g.D;
+  return P * (P + 1) * elem;
+}
+
+static size_t zip_elems(const Geometry& g, bool wm_in_smem) {
+  const size_t Dc = g.Dc, D = g.D, P = Dc * D;
+  return 2 * Dc * Dc * D + Dc * Dc * D * D + P * P + trunc_ws_elems((int)P, g.Dc, !wm_in_smem);
+}
+
+size_t boundary_slot_elems(const Geometry& g, bool wm_in_smem) {
+  const size_t envT = (size_t)g.Dc * g.D * g.Dc;
+  return zip_elems(g, wm_in_smem) + (size_t)g.Lx * envT;
+}
+
+__host__ __device__ inline size_t tmp_elems(const Geometry& g) {
+  const size_t Dc = g.Dc, D = g.D;
+  return Dc * Dc * D * D * D;
+}
+
+size_t row_slot_elems(const Geometry& g) {
+  const size_t envT = (size_t)g.Dc * g.D * g.Dc, D4 = (size_t)g.D * g.D * g.D * g.D;
+  return (size_t)(g.Lx + 1) * envT + 4 * envT + D4 + 2 * tmp_elems(g);
+}
+
+size_t pair_slot_elems(const Geometry& g) {
+  const size_t envT2 = (size_t)g.Dc * g.D * g.D * g.Dc;
+  return (size_t)(g.Lx + 1) * envT2 + 4 * envT2 + 2 * tmp_elems(g);
+}
+
+size_t mc_slot_elems(const Geometry& g, bool wm_in_smem) {
+  const size_t envT = (size_t)g.Dc * g.D * g.Dc;
+  const size_t sand = row_slot_elems(g) > pair_slot_elems(g) ? row_slot_elems(g) : pair_slot_elems(g);
+  return (size_t)g.Ly * g.Lx * envT + 2 * (size_t)g.Lx * envT + zip_elems(g, wm_in_smem) + sand;
+}
+
+// ------------------------------------------------------------ zip-up row
+// Absorbs row `row` (spins `sp`) into the boundary MPS `Min` (padded
+// [Lx][Dc][D][Dc], bond dims bdin), writing `Mout` (bond dims bdout).
+// dir 0: the MPS faces the row's up legs (top-down sweep); dir 1: down legs.
+// Returns ln of the norm divided out of the last tensor (Fig. 1d with the
+// per-row normalisation that keeps the log scale).
+template <typename R>
+struct ZipBufs {
+  R* C0;
+  R* C1;
+  R* Y;
+  R* X;
+  TruncWork<R> tw;
+};
+
+template <typename R>
+__device__ R absorb_row(const KArgs<R>& a, const R* Min, R* Mout, int row, int dir, bool lr, const int* bdin,
+                        const uint64_t* sp, ZipBufs<R>& zb, R* red) {
+  const Geometry& g = a.g;
+  const int D = g.D, Dc = g.Dc, Lx = g.Lx;
+  const int envT = Dc * D * Dc;
+  const int D3 = D * D * D, DD = D * D;
+  const int sl = D3, sr = DD;
+  const int si = dir == 0 ? D : 1, so = dir == 0 ? 1 : D;
+  for (int e = threadIdx.x; e < Lx * envT; e += blockDim.x) Mout[e] = R(0);
+  R* Cc = zb.C0;
+  R* Cn = zb.C1;
+  if (threadIdx.x == 0) Cc[0] = R(1);
+  __syncthreads();
+  int kcur = 1;
+  int last;
+  if (lr) {
+    for (int c = 0; c < Lx; ++c) {
+      const TDims td = tdims(g, row, c);
+      ZipDims z;
+      z.k = kcur; z.a = bdin[c]; z.b = bdin[c + 1];
+      z.i = dir == 0 ? td.u : td.d;
+      z.l = td.l; z.r = td.r;
+      z.o = dir == 0 ? td.d : td.u;
+      const R* T = tptr(a, row * Lx + c, spin_of(sp, row * Lx + c));
+      cta_gemm<R>(zip_lr_step(0, z, D, Dc, sl, sr, si, so), Cc, Min + (size_t)c * envT, zb.Y, false);
+      __syncthreads();
+      cta_gemm<R>(zip_lr_step(1, z, D, Dc, sl, sr, si, so), zb.Y, T, zb.X, false);
+      __syncthreads();
+      const int m = z.k * z.o, n = z.b * z.r;
+      if (c < Lx - 1) {
+        const int K = min(Dc, min(m, n));
+        cta_topk_left<R>(zb.X, m, n, K, zb.tw, Mout + (size_t)c * envT, ix2(z.o, D * Dc, Dc), ix1(1), Cn,
+                         ix1(n), ix1(1));
+        R* t = Cc; Cc = Cn; Cn = t;
+        kcur = K;
+      } else {
+        for (int e = threadIdx.x; e < m; e += blockDim.x) {
+          const int k = e / z.o, o = e % z.o;
+          Mout[(size_t)c * envT + k * D * Dc + o * Dc] = zb.X[e];
+        }
+        __syncthreads();
+      }
+    }
+    last = Lx - 1;
+  } else {
+    for (int c = Lx - 1; c >= 0; --c) {
+      const TDims td = tdims(g, row, c);
+      ZipDims z;
+      z.k = kcur; z.a = bdin[c]; z.b = bdin[c + 1];
+      z.i = dir == 0 ? td.u : td.d;
+      z.l = td.l; z.r = td.r;
+      z.o = dir == 0 ? td.d : td.u;
+      const R* T = tptr(a, row * Lx + c, spin_of(sp, row * Lx + c));
+      cta_gemm<R>(zip_rl_step(0, z, D, Dc, sl, sr, si, so), Min + (size_t)c * envT, Cc, zb.Y, false);
+      __syncthreads();
+      cta_gemm<R>(zip_rl_step(1, z, D, Dc, sl, sr, si, so), zb.Y, T, zb.X, false);
+      __syncthreads();
+      const int m = z.o * z.k, n = z.a * z.l;
+      if (c > 0) {
+        const int K = min(Dc, min(m, n));
+        cta_topk_left<R>(zb.X, m, n, K, zb.tw, Mout + (size_t)c * envT, ix2(z.k, Dc, 1), ix1(D * Dc), Cn,
+                         ix1(1), ix1(K));
+        R* t = Cc; Cc = Cn; Cn = t;
+        kcur = K;
+      } else {
+        for (int e = threadIdx.x; e < m; e += blockDim.x) {
+          const int o = e / z.k, k = e % z.k;
+          Mout[o * Dc + k] = zb.X[e];
+        }
+        __syncthreads();
+      }
+    }
+    last = 0;
+  }
+  R ss = R(0);
+  R* Ml = Mout + (size_t)last * envT;
+  for (int e = threadIdx.x; e < envT; e += blockDim.x) ss += Ml[e] * Ml[e];
+  ss = block_sum(ss, red);
+  const R nrm = dsqrt(ss);
+  if (nrm > R(0)) {
+    const R inv = R(1) / nrm;
+    for (int e = threadIdx.x; e < envT; e += blockDim.x) Ml[e] *= inv;
+  }
+  __syncthreads();
+  return nrm;
+}
+
+template <typename R>
+__device__ void carve_zip(const Geometry& g, R*& p, ZipBufs<R>& zb, R* wm_smem, R* red) {
+  const size_t Dc = g.Dc, D = g.D, P = Dc * D;
+  zb.C0 = p; p += Dc * Dc * D;
+  zb.C1 = p; p += Dc * Dc * D;
+  zb.Y = p; p += Dc * Dc * D * D;
+  zb.X = p; p += P * P;
+  TruncWork<R>& w = zb.tw;
+  w.ldw = (int)P + 1;
+  if (wm_smem) {
+    w.Wm = wm_smem;
+  } else {
+    w.Wm = p; p += P * (P + 1);
+  }
+  w.Qmax = (int)P;
+  w.tau = p; p += 2 * P;
+  w.t = p; p += 2 * P;
+  w.t2 = p; p += 2 * P;
+  w.lam = p; p += Dc;
+  w.Z = p; p += Dc * 2 * P;
+  w.lu = p; p += Dc * 6 * 2 * P;
+  w.Ub = p; p += P * Dc;
+  w.Uk = p; p += P * Dc;
+  p += 64;
+  w.red = red;
+}
+
+// ------------------------------------------------------------ k_boundary
+template <typename R>
+__global__ void __launch_bounds__(kThreads) k_boundary(KArgs<R> a, int dirs) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ R red[64];
+  __shared__ uint64_t sp[kMaxWords];
+  __shared__ int ones[kMaxDcD + 1];
+  const Geometry& g = a.g;
+  const int Lx = g.Lx, Ly = g.Ly, Dc = g.Dc, D = g.D;
+  const size_t envT = (size_t)Dc * D * Dc;
+  R* p = a.scratch + (size_t)blockIdx.x * a.slot_elems;
+  ZipBufs<R> zb;
+  carve_zip<R>(g, p, zb, a.smem_wm ? reinterpret_cast<R*>(smem_raw) : nullptr, red);
+  R* lastbuf = p;
+  for (int i = threadIdx.x; i <= Lx; i += blockDim.x) ones[i] = 1;
+  for (int item = blockIdx.x; item < a.n * dirs; item += gridDim.x) {
+    const int cfg = item / dirs, dir = item % dirs;
+    __syncthreads();
+    for (int i = threadIdx.x; i < g.nwords; i += blockDim.x) sp[i] = a.S[(size_t)cfg * g.nwords + i];
+    __syncthreads();
+    const R* Min = a.triv_mps;
+    double ls = 0.0;
+    bool zero = false;
+    for (int j = 0; j < Ly; ++j) {
+      const int r = dir == 0 ? j : Ly - 1 - j;
+      if (dir == 1 && r == 0) break;
+      R* Mout;
+      if (dir == 0) Mout = r <= Ly - 2 ? a.envU + ((size_t)cfg * Ly + r) * Lx * envT : lastbuf;
+      else Mout = a.envL + ((size_t)cfg * Ly + r) * Lx * envT;
+      const int* bdin = j == 0 ? ones : a.bd + ((size_t)dir * Ly + (j - 1)) * (Lx + 1);
+      const R nrm = absorb_row<R>(a, Min, Mout, r, dir, (j % 2) == 0, bdin, sp, zb, red);
+      if (!(nrm > R(0))) zero = true;
+      else ls += log((double)nrm);
+      Min = Mout;
+    }
+    if (dir == 0) {
+      // All physical legs are one now: close the chain of matrices M_c[:, 0, :].
+      __shared__ R vec[kMaxDc], nv[kMaxDc];
+      if (threadIdx.x == 0) {
+        const int* bdl = a.bd + ((size_t)0 * Ly + (Ly - 1)) * (Lx + 1);
+        vec[0] = R(1);
+        int na = 1;
+        for (int c = 0; c < Lx; ++c) {
+          const int nb = bdl[c + 1];
+          const R* M = lastbuf + (size_t)c * envT;
+          for (int b = 0; b < nb; ++b) {
+            R s = R(0);
+            for (int x = 0; x < na; ++x) s += vec[x] * M[(size_t)x * D * Dc + b];
+            nv[b] = s;
+          }
+          for (int b = 0; b < nb; ++b) vec[b] = nv[b];
+          na = nb;
+        }
+        const R v = vec[0];
+        if (zero || v == R(0)) {
+          a.logabs[cfg] = -INFINITY;
+          a.sign[cfg] = 0;
+          atomicOr(&a.flags[cfg], kFlagZeroW);
+        } else {
+          a.logabs[cfg] = ls + log(fabs((double)v));
+          a.sign[cfg] = v > R(0) ? 1 : -1;
+        }
+      }
+    } else if (zero && threadIdx.x == 0) {
+      atomicOr(&a.flags[cfg], kFlagZeroW);
+    }
+  }
+}
+
+template <typename R>
+__device__ R block_dot(const R* x, const R* y, int n, R* red) {
+  R s = R(0);
+  for (int e = threadIdx.x; e < n; e += blockDim.x) s += x[e] * y[e];
+  return block_sum(s, red);
+}
+
+// ----------------------------------------------------------------- k_row
+template <typename R>
+__global__ void __launch_bounds__(kThreads) k_row(KArgs<R> a) {
+  __shared__ R red[64];
+  __shared__ uint64_t sp[kMaxWords];
+  const Geometry& g = a.g;
+  const int Lx = g.Lx, Ly = g.Ly, Dc = g.Dc, D = g.D;
+  const int envT = Dc * D * Dc, D4 = D * D * D * D;
+  R* p = a.scratch + (size_t)blockIdx.x * a.slot_elems;
+  R* Gb = p; p += (size_t)(Lx + 1) * envT;
+  R* F0 = p; p += envT;
+  R* F1 = p; p += envT;
+  R* X1 = p; p += envT;
+  R* X2 = p; p += envT;
+  R* Bb = p; p += D4;
+  R* t0 = p; p += tmp_elems(g);
+  R* t1 = p;
+  for (int item = blockIdx.x; item < a.n * Ly; item += gridDim.x) {
+    const int cfg = item / Ly, r = item % Ly;
+    __syncthreads();
+    for (int i = threadIdx.x; i < g.nwords; i += blockDim.x) sp[i] = a.S[(size_t)cfg * g.nwords + i];
+    for (int e = threadIdx.x; e < envT; e += blockDim.x) Gb[(size_t)Lx * envT + e] = a.triv_t1[e];
+    __syncthreads();
+    const R* Mu = r == 0 ? a.triv_mps : a.envU + ((size_t)cfg * Ly + (r - 1)) * Lx * envT;
+    const R* Md = r == Ly - 1 ? a.triv_mps : a.envL + ((size_t)cfg * Ly + (r + 1)) * Lx * envT;
+    for (int c = Lx - 1; c >= 0; --c) {
+      const int site = r * Lx + c;
+      run_op<R>(OP_COL1_RIGHT, D, Dc, Gb + (size_t)(c + 1) * envT, Mu + (size_t)c * envT,
+                tptr(a, site, spin_of(sp, site)), Md + (size_t)c * envT, nullptr, Gb + (size_t)c * envT, t0, t1);
+    }
+    const R W = Gb[0];
+    const bool ok = W != R(0);
+    double eh = 0.0;
+    const R* F = a.triv_t1;
+    R* Fn = F0;
+    for (int c = 0; c < Lx; ++c) {
+      const int site = r * Lx + c;
+      const int s = spin_of(sp, site);
+      if (a.O != nullptr) {
+        run_op<R>(OP_SITE_ENV, D, Dc, F, Mu + (size_t)c * envT, Md + (size_t)c * envT,
+                  Gb + (size_t)(c + 1) * envT, nullptr, Bb, t0, t1);
+        R* Oo = a.O + ((size_t)cfg * g.N + site) * D4;
+        const R inv = ok ? R(1) / W : R(0);
+        for (int e = threadIdx.x; e < D4; e += blockDim.x) Oo[e] = Bb[e] * inv;
+      }
+      if (c < Lx - 1) {
+        const int s2 = spin_of(sp, site + 1);
+        if (s != s2) {
+          run_op<R>(OP_COL1_LEFT, D, Dc, F, Mu + (size_t)c * envT, tptr(a, site, s2), Md + (size_t)c * envT,
+                    nullptr, X1, t0, t1);
+          run_op<R>(OP_COL1_LEFT, D, Dc, X1, Mu + (size_t)(c + 1) * envT, tptr(a, site + 1, s),
+                    Md + (size_t)(c + 1) * envT, nullptr, X2, t0, t1);
+          const R wp = block_dot(X2, Gb + (size_t)(c + 2) * envT, envT, red);
+          if (ok) eh += 0.5 * g.J1 * ((double)wp / (double)W);
+        }
+        run_op<R>(OP_COL1_LEFT, D, Dc, F, Mu + (size_t)c * envT, tptr(a, site, s), Md + (size_t)c * envT,
+                  nullptr, Fn, t0, t1);
+        F = Fn;
+        Fn = (Fn == F0) ? F1 : F0;
+      }
+    }
+    if (threadIdx.x == 0) {
+      a.eloc_h[(size_t)cfg * Ly + r] = eh;
+      a.w_row[(size_t)cfg * Ly + r] = (double)W;
+      if (!ok) atomicOr(&a.flags[cfg], kFlagZeroW);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- k_pair
+template <typename R>
+__global__ void __launch_bounds__(kThreads) k_pair(KArgs<R> a) {
+  __shared__ R red[64];
+  __shared__ uint64_t sp[kMaxWords];
+  const Geometry& g = a.g;
+  const int Lx = g.Lx, Ly = g.Ly, Dc = g.Dc, D = g.D;
+  const int envT = Dc * D * Dc, envT2 = Dc * D * D * Dc;
+  R* p = a.scratch + (size_t)blockIdx.x * a.slot_elems;
+  R* Hb = p; p += (size_t)(Lx + 1) * envT2;
+  R* E0 = p; p += envT2;
+  R* E1 = p; p += envT2;
+  R* X1 = p; p += envT2;
+  R* X2 = p; p += envT2;
+  R* t0 = p; p += tmp_elems(g);
+  R* t1 = p;
+  const int npairs = Ly - 1;
+  for (int item = blockIdx.x; item < a.n * npairs; item += gridDim.x) {
+    const int cfg = item / npairs, r = item % npairs;
+    __syncthreads();
+    for (int i = threadIdx.x; i < g.nwords; i += blockDim.x) sp[i] = a.S[(size_t)cfg * g.nwords + i];
+    for (int e = threadIdx.x; e < envT2; e += blockDim.x) Hb[(size_t)Lx * envT2 + e] = a.triv_t2[e];
+    __syncthreads();
+    const R* Mu = r == 0 ? a.triv_mps : a.envU + ((size_t)cfg * Ly + (r - 1)) * Lx * envT;
+    const R* Md = r + 2 > Ly - 1 ? a.triv_mps : a.envL + ((size_t)cfg * Ly + (r + 2)) * Lx * envT;
+    for (int c = Lx - 1; c >= 0; --c) {
+      const int s1 = r * Lx + c, s2 = (r + 1) * Lx + c;
+      run_op<R>(OP_COL2_RIGHT, D, Dc, Hb + (size_t)(c + 1) * envT2, Mu + (size_t)c * envT,
+                tptr(a, s1, spin_of(sp, s1)), tptr(a, s2, spin_of(sp, s2)), Md + (size_t)c * envT,
+                Hb + (size_t)c * envT2, t0, t1);
+    }
+    const R W = Hb[0];
+    const bool ok = W != R(0);
+    double ev = 0.0;
+    const R* E = a.triv_t2;
+    R* En = E0;
+    for (int c = 0; c < Lx; ++c) {
+      const int i1 = r * Lx + c, i2 = (r + 1) * Lx + c;
+      const int a1 = spin_of(sp, i1), a2 = spin_of(sp, i2);
+      const R* Muc = Mu + (size_t)c * envT;
+      const R* Mdc = Md + (size_t)c * envT;
+      if (a1 != a2) {  // vertical pair (r,c)-(r+1,c)
+        run_op<R>(OP_COL2_LEFT, D, Dc, E, Muc, tptr(a, i1, a2), tptr(a, i2, a1), Mdc, X1, t0, t1);
+        const R wp = block_dot(X1, Hb + (size_t)(c + 1) * envT2, envT2, red);
+        if (ok) ev += 0.5 * g.J1 * ((double)wp / (double)W);
+      }
+      if (c < Lx - 1 && g.J2 != 0.0) {
+        const int j1 = i1 + 1, j2 = i2 + 1;
+        const int b1 = spin_of(sp, j1), b2 = spin_of(sp, j2);
+        const R* Mun = Mu + (size_t)(c + 1) * envT;
+        const R* Mdn = Md + (size_t)(c + 1) * envT;
+        if (a1 != b2) {  // diagonal (r,c)-(r+1,c+1)
+          run_op<R>(OP_COL2_LEFT, D, Dc, E, Muc, tptr(a, i1, b2), tptr(a, i2, a2), Mdc, X1, t0, t1);
+          run_op<R>(OP_COL2_LEFT, D, Dc, X1, Mun, tptr(a, j1, b1), tptr(a, j2, a1), Mdn, X2, t0, t1);
+          const R wp = block_dot(X2, Hb + (size_t)(c + 2) * envT2, envT2, red);
+          if (ok) ev += 0.5 * g.J2 * ((double)wp / (double)W);
+        }
+        if (b1 != a2) {  // anti-diagonal (r,c+1)-(r+1,c)
+          run_op<R>(OP_COL2_LEFT, D, Dc, E, Muc, tptr(a, i1, a1), tptr(a, i2, b1), Mdc, X1, t0, t1);
+          run_op<R>(OP_COL2_LEFT, D, Dc, X1, Mun, tptr(a, j1, a2), tptr(a, j2, b2), Mdn, X2, t0, t1);
+          const R wp = block_dot(X2, Hb + (size_t)(c + 2) * envT2, envT2, red);
+          if (ok) ev += 0.5 * g.J2 * ((double)wp / (double)W);
+        }
+      }
+      if (c < Lx - 1) {
+        run_op<R>(OP_COL2_LEFT, D, Dc, E, Muc, tptr(a, i1, a1), tptr(a, i2, a2), Mdc, En, t0, t1);
+        E = En;
+        En = (En == E0) ? E1 : E0;
+      }
+    }
+    if (threadIdx.x == 0) {
+      a.eloc_v[(size_t)cfg * Ly + r] = ev;
+      if (!ok) atomicOr(&a.flags[cfg], kFlagZeroW);
+    }
+  }
+}
+
+// ------------------------------------------------------------ k_finalize
+// E(S) = sum over bonds of J (+1/4 parallel, -1/4 antiparallel) plus the
+// exchange terms already summed per row / row pair.  Status: S^z != 0 ->
+// invalid (1), zero amplitude -> numeric (5).
+__global__ void k_finalize(Geometry g, const uint64_t* S, int n, const double* eloc_h, const double* eloc_v,
+                           const int* flags, double* eloc, int* status, int have_eloc) {
+  const int cfg = blockIdx.x * blockDim.x + threadIdx.x;
+  if (cfg >= n) return;
+  const uint64_t* sp = S + (size_t)cfg * g.nwords;
+  int pc = 0;
+  for (int w = 0; w < g.nwords; ++w) {
+    uint64_t word = sp[w];
+    if (w == g.nwords - 1 && (g.N & 63)) word &= (1ull << (g.N & 63)) - 1ull;
+    pc += __popcll(word);
+  }
+  int st = 0;
+  if ((g.N % 2 == 0) && pc != g.N / 2) st = 1;
+  else if (flags[cfg] & kFlagZeroW) st = 5;
+  if (status) status[cfg] = st;
+  if (!have_eloc || eloc == nullptr) return;
+  double e = 0.0;
+  const int Lx = g.Lx, Ly = g.Ly;
+  for (int r = 0; r < Ly; ++r)
+    for (int c = 0; c < Lx; ++c) {
+      const int i = r * Lx + c, si = spin_of(sp, i);
+      if (c + 1 < Lx) e += (si == spin_of(sp, i + 1) ? 0.25 : -0.25) * g.J1;
+      if (r + 1 < Ly) e += (si == spin_of(sp, i + Lx) ? 0.25 : -0.25) * g.J1;
+      if (r + 1 < Ly && c + 1 < Lx) e += (si == spin_of(sp, i + Lx + 1) ? 0.25 : -0.25) * g.J2;
+      if (r + 1 < Ly && c + 1 < Lx) e += (spin_of(sp, i + 1) == spin_of(sp, i + Lx) ? 0.25 : -0.25) * g.J2;
+    }
+  for (int r = 0; r < Ly; ++r) e += eloc_h[(size_t)cfg * Ly + r];
+  for (int r = 0; r + 1 < Ly; ++r) e += eloc_v[(size_t)cfg * Ly + r];
+  eloc[cfg] = st == 0 ? e : NAN;
+}
+
+// ------------------------------------------------------- gradient sums
+// sumO[i][s][p] += sum_cfg O_cfg[i][p] [s_i == s], sumEO likewise times E.
+// Each thread owns elements (i, p) of both spin blocks, so no atomics.
+template <typename R>
+__global__ void k_grad_accum(GradArgs a, const R* __restrict__ O) {
+  const size_t total = (size_t)a.N * a.D4;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / a.D4), p = (int)(e % a.D4);
+    double o0 = 0, o1 = 0, eo0 = 0, eo1 = 0;
+    for (int cfg = 0; cfg < a.n; ++cfg) {
+      if (a.status[cfg] != 0) continue;
+      const double o = (double)O[(size_t)cfg * total + e];
+      const double E = a.eloc[cfg];
+      if (spin_of(a.S + (size_t)cfg * a.nwords, i)) {
+        o1 += o;
+        eo1 += E * o;
+      } else {
+        o0 += o;
+        eo0 += E * o;
+      }
+    }
+    const size_t b0 = ((size_t)i * 2) * a.D4 + p, b1 = b0 + a.D4;
+    a.sumO[b0] += o0;
+    a.sumO[b1] += o1;
+    a.sumEO[b0] += eo0;
+    a.sumEO[b1] += eo1;
+  }
+}
+
+// sums[0] += sum of E over configurations with status 0, sums[1] += their count.
+__global__ void k_sum_eloc(const double* eloc, const int* status, int n, double* sums) {
+  __shared__ double sh[2][kThreads];
+  double s = 0, c = 0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x)
+    if (status[i] == 0) {
+      s += eloc[i];
+      c += 1;
+    }
+  sh[0][threadIdx.x] = s;
+  sh[1][threadIdx.x] = c;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      sh[0][threadIdx.x] += sh[0][threadIdx.x + o];
+      sh[1][threadIdx.x] += sh[1][threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    sums[0] += sh[0][0];
+    sums[1] += sh[1][0];
+  }
+}
+
+// grad = 2 (<E O> - <E><O>), cov = grad / 2.
+__global__ void k_grad_finalize(int total, const double* sums, const double* sumO, const double* sumEO, double* grad,
+                                double* cov) {
+  const double n = sums[1];
+  const double Ebar = n > 0 ? sums[0] / n : 0.0;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+    const double c = n > 0 ? sumEO[e] / n - Ebar * (sumO[e] / n) : 0.0;
+    if (grad) grad[e] = 2.0 * c;
+    if (cov) cov[e] = c;
+  }
+}
+
+// ------------------------------------------------------------------- k_mc
+// SplitMix64 output function (Steele, Lea & Flood 2014), used as a
+// counter-based generator keyed by (seed, chain, sweep, bond).
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+__device__ __forceinline__ double sampler_uniform(uint64_t seed, uint64_t chain, uint64_t sweep, uint64_t bond) {
+  const uint64_t G = 0x9E3779B97F4A7C15ull;
+  uint64_t h = seed;
+  h = mix64(h + G * (1ull + chain));
+  h = mix64(h + G * (1ull + sweep));
+  h = mix64(h + G * (1ull + bond));
+  return (double)(h >> 11) * 0x1.0p-53;
+}
+
+// Metropolis sweeps (sampling with weight W^2, Sec. II) over nearest-neighbour
+// exchanges: horizontal bonds row by row, then vertical bonds row pair by row
+// pair.  Lower environments are rebuilt from the current S at the start of
+// each pass; the upper environment grows from the updated rows; the row (or
+// row-pair) transfers to the left are carried with the accepted spins.
+template <typename R>
+__global__ void __launch_bounds__(kThreads) k_mc(KArgs<R> a, uint64_t* S, int nsweeps, uint64_t seed, uint64_t chain0,
+                                                 uint64_t sweep0, long long* accepted) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ R red[64];
+  __shared__ uint64_t sp[kMaxWords];
+  __shared__ int ones[kMaxDcD + 1];
+  const Geometry& g = a.g;
+  const int Lx = g.Lx, Ly = g.Ly, Dc = g.Dc, D = g.D;
+  const size_t envT = (size_t)Dc * D * Dc, envT2 = envT * D;
+  R* p = a.scratch + (size_t)blockIdx.x * a.slot_elems;
+  R* envL = p; p += (size_t)Ly * Lx * envT;
+  R* Ubuf[2];
+  Ubuf[0] = p; p += (size_t)Lx * envT;
+  Ubuf[1] = p; p += (size_t)Lx * envT;
+  ZipBufs<R> zb;
+  carve_zip<R>(g, p, zb, a.smem_wm ? reinterpret_cast<R*>(smem_raw) : nullptr, red);
+  R* Hb = p; p += (size_t)(Lx + 1) * envT2;
+  R* Q[4];
+  for (int q = 0; q < 4; ++q) { Q[q] = p; p += envT2; }
+  R* t0 = p; p += tmp_elems(g);
+  R* t1 = p;
+  for (int i = threadIdx.x; i <= Lx; i += blockDim.x) ones[i] = 1;
+  const int nh = Ly * (Lx - 1);
+  for (int chain = blockIdx.x; chain < a.n; chain += gridDim.x) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < g.nwords; i += blockDim.x) sp[i] = S[(size_t)chain * g.nwords + i];
+    __syncthreads();
+    long long acc = 0;
+    for (int k = 0; k < nsweeps; ++k) {
+      const uint64_t sweep = sweep0 + (uint64_t)k;
+      for (int pass = 0; pass < 2; ++pass) {
+        // lower environments L_r, r = Ly-1 .. 1, from the current S
+        const R* Min = a.triv_mps;
+        for (int j = 0; j + 1 < Ly; ++j) {
+          const int r = Ly - 1 - j;
+          const int* bdin = j == 0 ? ones : a.bd + ((size_t)1 * Ly + (j - 1)) * (Lx + 1);
+          R* Mout = envL + (size_t)r * Lx * envT;
+          absorb_row<R>(a, Min, Mout, r, 1, (j % 2) == 0, bdin, sp, zb, red);
+          Min = Mout;
+        }
+        const R* Mu = a.triv_mps;
+        int ub = 0;
+        const int rows = pass == 0 ? Ly : Ly - 1;
+        for (int r = 0; r < rows; ++r) {
+          const R* Md;
+          if (pass == 0) Md = r == Ly - 1 ? a.triv_mps : envL + (size_t)(r + 1) * Lx * envT;
+          else Md = r + 2 > Ly - 1 ? a.triv_mps : envL + (size_t)(r + 2) * Lx * envT;
+          const size_t tsz = pass == 0 ? envT : envT2;
+          const R* triv = pass == 0 ? a.triv_t1 : a.triv_t2;
+          for (size_t e = threadIdx.x; e < tsz; e += blockDim.x) Hb[(size_t)Lx * tsz + e] = triv[e];
+          __syncthreads();
+          for (int c = Lx - 1; c >= 0; --c) {
+            const int i1 = r * Lx + c;
+            if (pass == 0)
+              run_op<R>(OP_COL1_RIGHT, D, Dc, Hb + (size_t)(c + 1) * tsz, Mu + (size_t)c * envT,
+                        tptr(a, i1, spin_of(sp, i1)), Md + (size_t)c * envT, nullptr, Hb + (size_t)c * tsz, t0, t1);
+            else
+              run_op<R>(OP_COL2_RIGHT, D, Dc, Hb + (size_t)(c + 1) * tsz, Mu + (size_t)c * envT,
+                        tptr(a, i1, spin_of(sp, i1)), tptr(a, i1 + Lx, spin_of(sp, i1 + Lx)),
+                        Md + (size_t)c * envT, Hb + (size_t)c * tsz, t0, t1);
+          }
+          const R* E = triv;
+          int e = 3;   // index in Q of the buffer E lives in (none yet)
+          const int ncol = pass == 0 ? Lx - 1 : Lx;
+          for (int c = 0; c < ncol; ++c) {
+            const int i1 = r * Lx + c;
+            const int i2 = pass == 0 ? i1 + 1 : i1 + Lx;
+            const int s1 = spin_of(sp, i1), s2 = spin_of(sp, i2);
+            R* X1 = Q[(e + 1) & 3];
+            R* Xf = Q[(e + 2) & 3];
+            R* X2 = Q[(e + 3) & 3];
+            const R* Muc = Mu + (size_t)c * envT;
+            const R* Mdc = Md + (size_t)c * envT;
+            int chosen;
+            if (s1 != s2) {
+              R w, wp;
+              if (pass == 0) {
+                run_op<R>(OP_COL1_LEFT, D, Dc, E, Muc, tptr(a, i1, s1), Mdc, nullptr, X1, t0, t1);
+                run_op<R>(OP_COL1_LEFT, D, Dc, E, Muc, tptr(a, i1, s2), Mdc, nullptr, Xf, t0, t1);
+                run_op<R>(OP_COL1_LEFT, D, Dc, Xf, Mu + (size_t)(c + 1) * envT, tptr(a, i2, s1),
+                          Md + (size_t)(c + 1) * envT, nullptr, X2, t0, t1);
+                w = block_dot(X1, Hb + (size_t)(c + 1) * tsz, (int)tsz, red);
+                wp = block_dot(X2, Hb + (size_t)(c + 2) * tsz, (int)tsz, red);
+              } else {
+                run_op<R>(OP_COL2_LEFT, D, Dc, E, Muc, tptr(a, i1, s1), tptr(a, i2, s2), Mdc, X1, t0, t1);
+                run_op<R>(OP_COL2_LEFT, D, Dc, E, Muc, tptr(a, i1, s2), tptr(a, i2, s1), Mdc, Xf, t0, t1);
+                w = block_dot(X1, Hb + (size_t)(c + 1) * tsz, (int)tsz, red);
+                wp = block_dot(Xf, Hb + (size_t)(c + 1) * tsz, (int)tsz, red);
+              }
+              const uint64_t bond = pass == 0 ? (uint64_t)(r * (Lx - 1) + c) : (uint64_t)(nh + r * Lx + c);
+              const double u = sampler_uniform(seed, chain0 + (uint64_t)chain, sweep, bond);
+              bool take;
+              if (w == R(0)) {
+                take = true;
+              } else {
+                const double ratio = (double)wp / (double)w;
+                take = u < ratio * ratio;
+              }
+              if (take) {
+                if (threadIdx.x == 0) {
+                  sp[i1 >> 6] ^= 1ull << (i1 & 63);
+                  sp[i2 >> 6] ^= 1ull << (i2 & 63);
+                }
+                ++acc;
+                chosen = (e + 2) & 3;
+              } else {
+                chosen = (e + 1) & 3;
+              }
+              __syncthreads();
+            } else {
+              if (pass == 0)
+                run_op<R>(OP_COL1_LEFT, D, Dc, E, Muc, tptr(a, i1, s1), Mdc, nullptr, X1, t0, t1);
+              else
+                run_op<R>(OP_COL2_LEFT, D, Dc, E, Muc, tptr(a, i1, s1), tptr(a, i2, s2), Mdc, X1, t0, t1);
+              chosen = (e + 1) & 3;
+            }
+            e = chosen;
+            E = Q[e];
+          }
+          if (pass == 0 ? (r < Ly - 1) : true) {
+            const int* bdin = r == 0 ? ones : a.bd + ((size_t)0 * Ly + (r - 1)) * (Lx + 1);
+            absorb_row<R>(a, Mu, Ubuf[ub], r, 0, (r % 2) == 0, bdin, sp, zb, red);
+            Mu = Ubuf[ub];
+            ub ^= 1;
+          }
+        }
+      }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < g.nwords; i += blockDim.x) S[(size_t)chain * g.nwords + i] = sp[i];
+    if (threadIdx.x == 0 && accepted) accepted[chain] += acc;
+  }
+}
+
+// --------------------------------------------------------------- launchers
+template <typename R>
+int max_blocks_boundary(const Geometry& g) {
+  int dev = 0, nsm = 0, nb = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  size_t smem = wm_smem_bytes(g, sizeof(R));
+  if (smem > 160 * 1024) smem = 0;
+  if (smem) cudaFuncSetAttribute(k_boundary<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_boundary<R>, kThreads, smem);
+  if (nb < 1) nb = 1;
+  return nsm * nb;
+}
+
+template <typename R>
+cudaError_t launch_boundary(const KArgs<R>& a, int dirs, int grid, cudaStream_t st) {
+  const size_t smem = a.smem_wm ? wm_smem_bytes(a.g, sizeof(R)) : 0;
+  if (smem) {
+    cudaError_t e = cudaFuncSetAttribute(k_boundary<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k_boundary<R><<<grid, kThreads, smem, st>>>(a, dirs);
+  return cudaGetLastError();
+}
+
+template <typename R>
+int max_blocks_mc(const Geometry& g) {
+  int dev = 0, nsm = 0, nb = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  size_t smem = wm_smem_bytes(g, sizeof(R));
+  if (smem > 160 * 1024) smem = 0;
+  if (smem) cudaFuncSetAttribute(k_mc<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_mc<R>, kThreads, smem);
+  if (nb < 1) nb = 1;
+  return nsm * nb;
+}
+
+template <typename R>
+cudaError_t launch_mc(const KArgs<R>& a, uint64_t* S, int nsweeps, uint64_t seed, uint64_t chain0, uint64_t sweep0,
+                      long long* accepted, int grid, cudaStream_t st) {
+  const size_t smem = a.smem_wm ? wm_smem_bytes(a.g, sizeof(R)) : 0;
+  if (smem) {
+    cudaError_t e = cudaFuncSetAttribute(k_mc<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k_mc<R><<<grid, kThreads, smem, st>>>(a, S, nsweeps, seed, chain0, sweep0, accepted);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_row(const KArgs<R>& a, int grid, cudaStream_t st) {
+  k_row<R><<<grid, kThreads, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_pair(const KArgs<R>& a, int grid, cudaStream_t st) {
+  k_pair<R><<<grid, kThreads, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_grad_accum(const GradArgs& a, const R* O, cudaStream_t st) {
+  const size_t total = (size_t)a.N * a.D4;
+  int grid = (int)((total + kThreads - 1) / kThreads);
+  if (grid > 65535 * 8) grid = 65535 * 8;
+  k_grad_accum<R><<<grid, kThreads, 0, st>>>(a, O);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(const Geometry& g, const uint64_t* S, int n, const double* eloc_h, const double* eloc_v,
+                            const int* flags, double* eloc, int* status, int have_eloc, cudaStream_t st) {
+  k_finalize<<<(n + 127) / 128, 128, 0, st>>>(g, S, n, eloc_h, eloc_v, flags, eloc, status, have_eloc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sum_eloc(const double* eloc, const int* status, int n, double* sums, cudaStream_t st) {
+  k_sum_eloc<<<1, kThreads, 0, st>>>(eloc, status, n, sums);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_grad_finalize(int total, int, const double* sums, const double* sumO, const double* sumEO,
+                                 double* grad, double* cov, cudaStream_t st) {
+  int grid = (total + kThreads - 1) / kThreads;
+  if (grid > 65535) grid = 65535;
+  k_grad_finalize<<<grid, kThreads, 0, st>>>(total, sums, sumO, sumEO, grad, cov);
+  return cudaGetLastError();
+}
+
+#define PEPS_INST(R)                                                                                    \
+  template int max_blocks_boundary<R>(const Geometry&);                                                 \
+  template int max_blocks_mc<R>(const Geometry&);                                                       \
+  template cudaError_t launch_mc<R>(const KArgs<R>&, uint64_t*, int, uint64_t, uint64_t, uint64_t,      \
+                                    long long*, int, cudaStream_t);                                      \
+  template cudaError_t launch_boundary<R>(const KArgs<R>&, int, int, cudaStream_t);                     \
+  template cudaError_t launch_row<R>(const KArgs<R>&, int, cudaStream_t);                               \
+  template cudaError_t launch_pair<R>(const KArgs<R>&, int, cudaStream_t);                              \
+  template cudaError_t launch_grad_accum<R>(const GradArgs&, const R*, cudaStream_t);
+PEPS_INST(double)
+PEPS_INST(float)
+
+}  // namespace peps

@@ -1,0 +1,79 @@
+// Kernel arguments and launchers shared by the device code and the C ABI.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace peps {
+
+constexpr int kMaxWords = 64;        // up to 4096 sites
+constexpr int kMaxDc = 32;           // K <= 32 in the truncation
+constexpr int kMaxDcD = 256;         // Dc * D <= 256
+
+// Per-configuration status bits written by the kernels.
+constexpr int kFlagZeroW = 1;        // some W (psi, a row or a row pair) is exactly zero
+
+struct Geometry {
+  int Lx, Ly, D, Dc, N, nwords;
+  double J1, J2;
+};
+
+template <typename R>
+struct KArgs {
+  Geometry g;
+  const R* A;             // [N][2][D^4] padded site tensors
+  const R* triv_mps;      // [Lx][Dc*D*Dc] trivial boundary MPS (value 1)
+  const R* triv_t1;       // [Dc*D*Dc] trivial single-row transfer
+  const R* triv_t2;       // [Dc*D*D*Dc] trivial two-row transfer
+  const int* bd;          // [2][Ly][Lx+1] bond dimensions after absorbing j rows (per sweep)
+  const uint64_t* S;      // [n][nwords]
+  int n;
+  R* envU;                // [n][Ly][Lx][Dc*D*Dc] upper environments U_r
+  R* envL;                // [n][Ly][Lx][Dc*D*Dc] lower environments L_r
+  double* logabs;         // [n]
+  int8_t* sign;           // [n]
+  int* flags;             // [n]
+  double* eloc_h;         // [n][Ly]
+  double* eloc_v;         // [n][Ly]
+  double* w_row;          // [n][Ly] raw single-row sandwich values
+  R* O;                   // [n][N][D^4] or null
+  R* scratch;             // per-CTA slots
+  size_t slot_elems;
+  int smem_wm;            // 1 if the truncation matrix lives in dynamic shared memory
+};
+
+struct GradArgs {
+  int N, D4, nwords, n;
+  const uint64_t* S;
+  const double* eloc;
+  const int* status;
+  double* sumO;           // [N][2][D4]
+  double* sumEO;          // [N][2][D4]
+};
+
+// Slot sizes (elements) of each kernel's per-CTA scratch.
+size_t boundary_slot_elems(const Geometry& g, bool wm_in_smem);
+size_t row_slot_elems(const Geometry& g);
+size_t pair_slot_elems(const Geometry& g);
+size_t mc_slot_elems(const Geometry& g, bool wm_in_smem);
+size_t wm_smem_bytes(const Geometry& g, size_t elem);
+
+template <typename R> cudaError_t launch_boundary(const KArgs<R>& a, int dirs, int grid, cudaStream_t st);
+template <typename R> cudaError_t launch_row(const KArgs<R>& a, int grid, cudaStream_t st);
+template <typename R> cudaError_t launch_pair(const KArgs<R>& a, int grid, cudaStream_t st);
+template <typename R> cudaError_t launch_mc(const KArgs<R>& a, uint64_t* S, int nsweeps, uint64_t seed,
+                                            uint64_t chain0, uint64_t sweep0, long long* accepted,
+                                            int grid, cudaStream_t st);
+template <typename R> int max_blocks_boundary(const Geometry& g);
+template <typename R> int max_blocks_mc(const Geometry& g);
+template <typename R> cudaError_t launch_grad_accum(const GradArgs& a, const R* O, cudaStream_t st);
+
+cudaError_t launch_finalize(const Geometry& g, const uint64_t* S, int n, const double* eloc_h,
+                            const double* eloc_v, const int* flags, double* eloc, int* status,
+                            int have_eloc, cudaStream_t st);
+cudaError_t launch_grad_finalize(int total, int n_ok_dev_unused, const double* sums, const double* sumO,
+                                 const double* sumEO, double* grad, double* cov, cudaStream_t st);
+cudaError_t launch_sum_eloc(const double* eloc, const int* status, int n, double* sums, cudaStream_t st);
+
+}  // namespace peps

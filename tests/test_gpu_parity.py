@@ -1,0 +1,186 @@
+"""GPU parity: libpeps.so (through the C ABI) against the FP64 oracle.
+
+Tolerances (from the arithmetic; see the design notes):
+  FP64 path: ln|psi| within 1e-10 (relative error of psi <= 1e-10), same sign;
+             E_loc within 1e-8 * (1 + sum of |terms|); Delta within 1e-8 relative
+             to its largest entry; gradient within 1e-8 relative to its norm.
+  FP32 path: ln|psi| within 1e-5, E_loc within 2e-3 * (1 + sum|terms|),
+             gradient cosine similarity >= 0.999.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import peps_oracle as O
+from paper_1611_09467_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1611_09467_gb300 import build
+    build.build()
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+
+
+def make(A, L, Ly, D, Dc, J2, prec):
+    from paper_1611_09467_gb300.peps import PEPS
+    return PEPS(A, L, Ly, D, Dc, J1=1.0, J2=J2, prec=prec)
+
+
+def packed(spins):
+    return torch.from_numpy(inputs.pack_spins(spins).view(np.int64)).cuda()
+
+
+def eloc_scale(ev, Ly, Lx, J1, J2, spins):
+    """1 + sum over bonds of |each term| of E(S): the scale rounding errors are relative to."""
+    s = 1.0
+    for i, j, J, _ in O.all_bonds(Ly, Lx, J1, J2):
+        s += abs(J) / 4
+        if spins[i] != spins[j]:
+            s += abs(J) / 2 * abs(ev.ratios[(i, j)])
+    return s
+
+
+def oracle_evals(A, spins, Ly, Lx, Dc, J2, want_O=True):
+    return [O.evaluate(A, s, Ly, Lx, Dc, 1.0, J2, want_O=want_O) for s in spins]
+
+
+CASES_FP64 = [
+    # (Ly, Lx, D, Dc, J2, n, bias, seed) -- 4x4 D=2 Dc=4 is the exact regime
+    (4, 4, 2, 4, 0.5, 64, False, inputs.SEED_BASE + 1),
+    (6, 6, 3, 4, 0.5, 12, False, 77),          # truncated: Dc < D^3
+    (3, 5, 2, 3, 0.5, 12, True, 78),           # rectangular, odd width, truncated
+    (5, 4, 3, 9, 0.0, 8, False, 79),           # J2 = 0, exact
+    (2, 6, 2, 2, 0.5, 10, False, 80),          # two rows only, truncated
+]
+
+
+@pytest.mark.parametrize("case", CASES_FP64)
+def test_fp64_parity(case):
+    Ly, Lx, D, Dc, J2, n, bias, seed = case
+    A = inputs.make_tensors(Ly, Lx, D, seed, bias_zero_index=bias)
+    spins = inputs.random_sz0(n, Ly * Lx, seed)
+    p = make(A, Lx, Ly, D, Dc, J2, "fp64")
+    r = p.evaluate(packed(spins), logabs=True, eloc=True, O=True)
+    torch.cuda.synchronize()
+    la = r["logabs"].cpu().numpy()
+    sg = r["sign"].cpu().numpy()
+    el = r["eloc"].cpu().numpy()
+    Og = r["O"].cpu().numpy()
+    st = r["status"].cpu().numpy()
+    evs = oracle_evals(A, spins, Ly, Lx, Dc, J2)
+    assert (st == 0).all()
+    for k, ev in enumerate(evs):
+        assert sg[k] == ev.sign, k
+        assert abs(la[k] - ev.logabs) < 1e-10, (k, la[k], ev.logabs)
+        scale = eloc_scale(ev, Ly, Lx, 1.0, J2, spins[k])
+        assert abs(el[k] - ev.eloc) < 1e-8 * scale, (k, el[k], ev.eloc)
+        ref = ev.O.reshape(Ly * Lx, -1)
+        assert np.abs(Og[k] - ref).max() < 1e-8 * np.abs(ref).max(), k
+    # gradient over the batch
+    g = p.gradient(packed(spins))
+    e_site, gref, cref, nref = O.gradient(evs, spins, Ly * Lx, D)
+    assert g["n_used"] == nref
+    assert abs(g["energy_per_site"] - e_site) < 1e-9 * (1 + abs(e_site))
+    gg = g["grad"].cpu().numpy()
+    assert np.linalg.norm(gg - gref) < 1e-8 * np.linalg.norm(gref)
+    assert np.allclose(g["cov"].cpu().numpy(), gg / 2)
+    p.close()
+
+
+def test_fp32_parity_8x8():
+    """The 8x8 D=4 Dc=8 workload (biased tensors), FP32 path, a sample of configurations."""
+    Ly = Lx = 8
+    D, Dc, J2 = 4, 8, 0.5
+    A, _ = inputs.workload_inputs("8x8_D4_Dc8", n=1)
+    spins = inputs.random_sz0(24, 64, inputs.SEED_BASE + 2)
+    p = make(A, Lx, Ly, D, Dc, J2, "fp32")
+    r = p.evaluate(packed(spins), logabs=True, eloc=True, O=True)
+    torch.cuda.synchronize()
+    la = r["logabs"].cpu().numpy()
+    el = r["eloc"].cpu().numpy()
+    Og = r["O"].cpu().numpy().astype(np.float64)
+    evs = oracle_evals(A, spins, Ly, Lx, Dc, J2)
+    for k, ev in enumerate(evs):
+        assert r["sign"][k].item() == ev.sign
+        assert abs(la[k] - ev.logabs) < 1e-5, (k, la[k] - ev.logabs)
+        scale = eloc_scale(ev, Ly, Lx, 1.0, J2, spins[k])
+        assert abs(el[k] - ev.eloc) < 2e-3 * scale, (k, el[k], ev.eloc)
+    g = p.gradient(packed(spins))
+    _, gref, _, _ = O.gradient(evs, spins, 64, D)
+    gg = g["grad"].cpu().numpy().ravel()
+    cos = gg @ gref.ravel() / (np.linalg.norm(gg) * np.linalg.norm(gref))
+    assert cos > 0.999, cos
+    p.close()
+
+
+def test_status_and_edge_cases():
+    Ly = Lx = 4
+    D, Dc = 2, 4
+    A = inputs.make_tensors(Ly, Lx, D, 5)
+    p = make(A, Lx, Ly, D, Dc, 0.5, "fp64")
+    # empty batch
+    S0 = torch.zeros((0, 1), dtype=torch.int64, device="cuda")
+    r = p.evaluate(S0)
+    assert r["logabs"].numel() == 0
+    # S^z != 0 -> EINVAL status
+    bad = np.zeros((1, 16), dtype=np.uint8)
+    bad[0, :3] = 1
+    r = p.evaluate(packed(bad))
+    assert r["status"].item() == 1
+    # a zero site tensor block -> zero amplitude -> ENUMERIC, excluded from the gradient
+    A2 = A.copy()
+    A2[5, 1] = 0.0
+    p2 = make(A2, Lx, Ly, D, Dc, 0.5, "fp64")
+    spins = inputs.random_sz0(16, 16, 9)
+    r = p2.evaluate(packed(spins))
+    st = r["status"].cpu().numpy()
+    hit = spins[:, 5] == 1
+    assert (st[hit] == 5).all() and (st[~hit] == 0).all()
+    assert np.isinf(r["logabs"].cpu().numpy()[hit]).all()
+    g = p2.gradient(packed(spins))
+    assert g["n_used"] == int((~hit).sum())
+    p.close()
+    p2.close()
+
+
+def test_invalid_parameters_rejected():
+    from paper_1611_09467_gb300.peps import PepsError
+    A = inputs.make_tensors(4, 4, 2, 5)
+    with pytest.raises(PepsError):
+        make(A, 4, 4, 2, 40, 0.5, "fp64")         # Dc > 32
+    A[0, 0, 1, 0, 0, 0] = 1.0                    # non-zero past the open left edge
+    with pytest.raises(PepsError):
+        make(A, 4, 4, 2, 4, 0.5, "fp64")
+
+
+@pytest.mark.parametrize("Ly,Lx,D,Dc", [(4, 4, 2, 4), (4, 5, 2, 3)])
+def test_mc_sweep_matches_oracle(Ly, Lx, D, Dc):
+    """Metropolis sweeps, FP64: final configurations and accepted counts equal the
+    oracle's, except chains where a decision sat within 1e-9 of the threshold."""
+    A = inputs.make_tensors(Ly, Lx, D, 31)
+    n = 16
+    spins = inputs.random_sz0(n, Ly * Lx, 32)
+    p = make(A, Lx, Ly, D, Dc, 0.5, "fp64")
+    S = packed(spins)
+    acc = p.mc_sweep(S, nsweeps=2, seed=1234, chain0=100, sweep0=7)
+    torch.cuda.synchronize()
+    got = inputs.unpack_spins(S.cpu().numpy().view(np.uint64), Ly * Lx)
+    acc = acc.cpu().numpy()
+    mism = 0
+    for k in range(n):
+        s = spins[k].copy()
+        a_tot = 0
+        for sw in range(2):
+            s, a = O.mc_sweep(A, s, Ly, Lx, Dc, seed=1234, chain=100 + k, sweep=7 + sw)
+            a_tot += a
+        if not ((got[k] == s).all() and acc[k] == a_tot):
+            mism += 1
+        assert got[k].sum() == Ly * Lx // 2
+    assert mism == 0, mism
+    p.close()
