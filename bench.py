@@ -1,0 +1,304 @@
+"""Throughput of the PEPS sampling hot path on GB300.
+
+One step = one pass of the whole path over one batch: for every configuration
+ln|psi| and sign (boundary-MPS contraction, Fig. 1d), E_loc (Sec. II with the
+J1-J2 Hamiltonian of Sec. IV), Delta = dln psi/dA (Sec. II), and the device
+reductions to the energy and the gradient estimator 2(<E Delta> - <E><Delta>).
+
+Default workload: 16x16 open lattice, D = 8, Dc = 16, J2/J1 = 0.5, 16384
+configurations per step (per GPU), synthetic tensors and configurations.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line on rank 0.  Under torchrun each rank takes its own batch
+(weak scaling, no data-path collective); the time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1611_09467_gb300 import inputs  # noqa: E402
+
+METRIC = "configs/s (psi+E_loc+dln psi) 16x16 D=8 Dc=16, mixed vs plain FP32; p99 ms"
+UNIT = "configs/s"
+FP32_SIMT_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="16x16_D8_Dc16")
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--n", type=int, default=0, help="batch override (probes only; the metric uses the default)")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------ CPU oracle arm
+
+def _oracle_worker(args):
+    name, k = args
+    from oracle import peps_oracle as O
+    w = inputs.WORKLOADS[name]
+    A, spins = inputs.workload_inputs(name, n=1, first=k)
+    t = time.perf_counter()
+    O.evaluate(A, spins[0], w["L"], w["L"], w["Dc"], 1.0, w["J2"], want_O=True)
+    return time.perf_counter() - t
+
+
+def cpu_oracle_rate(name, seconds):
+    """Oracle configs/s on the host cores: one single-threaded worker per core
+    (spawned), each evaluating whole configurations, for about `seconds`."""
+    import multiprocessing as mp
+    for v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[v] = "1"
+    cores = os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        # probe one configuration per worker, then size the sample to ~seconds
+        t0 = time.perf_counter()
+        per = pool.map(_oracle_worker, [(name, 10_000 + i) for i in range(cores)])
+        t_probe = time.perf_counter() - t0
+        per_cfg = statistics.median(per)
+        rounds = max(1, int(seconds / max(per_cfg, 1e-3)))
+        ncfg = rounds * cores
+        t0 = time.perf_counter()
+        pool.map(_oracle_worker, [(name, 20_000 + i) for i in range(ncfg)])
+        wall = time.perf_counter() - t0
+    return dict(value=ncfg / wall, unit=UNIT, cores=cores, kind="oracle",
+                sample=f"{ncfg} configurations of the {name} workload, FP64 numpy oracle, "
+                       f"{cores} spawned single-threaded workers, {wall:.1f} s (probe {t_probe:.1f} s)")
+
+
+# ------------------------------------------------------------- clock sampler
+
+def start_clock_sampler(path):
+    q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    try:
+        f = open(path, "w")
+        return subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits", "-lms", "200"],
+                                stdout=f, stderr=subprocess.DEVNULL), f
+    except Exception:
+        return None, None
+
+
+def read_clocks(path, dev_index):
+    sm, mx, reasons = [], [], set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    try:
+        for line in open(path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9 or parts[0] != str(dev_index):
+                continue
+            sm.append(float(parts[1]))
+            mx.append(float(parts[2]))
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+    except Exception:
+        pass
+    if not sm:
+        return None
+    return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------- ours
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_1611_09467_gb300 import build, flops
+    from paper_1611_09467_gb300.peps import PEPS
+
+    build.build()
+    torch.cuda.set_device(local_rank)
+    w = inputs.WORKLOADS[args.workload]
+    L, D, Dc, J2 = w["L"], w["D"], w["Dc"], w["J2"]
+    n = args.n or w["n"]
+    A, _ = inputs.workload_inputs(args.workload, n=1)
+    # each rank draws its own configurations (weak scaling)
+    spins = inputs.random_sz0(n, L * L, inputs.SEED_BASE + w["cfg"], first=rank * n)
+    S_host = torch.from_numpy(inputs.pack_spins(spins).view(np.int64)).pin_memory()
+    S = S_host.cuda()
+    p = PEPS(A, L, L, D, Dc, J1=1.0, J2=J2, prec=args.prec)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        return p.gradient(S)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    p.profile_read(reset=True)
+    p.profile(True)
+    clk_path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv")
+    os.makedirs(os.path.dirname(clk_path), exist_ok=True)
+    sampler, fh = start_clock_sampler(clk_path)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    step_ms = []
+    ev0.record(stream)
+    for _ in range(args.steps):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        out = step()
+        b.record(stream)
+        step_ms.append((a, b))
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    if sampler:
+        sampler.terminate()
+        sampler.wait()
+        fh.close()
+    total_ms = ev0.elapsed_time(ev1)
+    per_step = [x.elapsed_time(y) for x, y in step_ms]
+    prof = p.profile_read(reset=True)
+    p.profile(False)
+    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    total_ms = float(t.item())
+    clocks = read_clocks(clk_path, local_rank)
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        la_h = torch.empty(n, dtype=torch.float64).pin_memory()
+        el_h = torch.empty(n, dtype=torch.float64).pin_memory()
+        torch.cuda.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(args.steps):
+            Sd = S_host.to("cuda", non_blocking=True)
+            o = p.gradient(Sd, per_config=True)
+            la_h.copy_(o["logabs"], non_blocking=True)
+            el_h.copy_(o["eloc"], non_blocking=True)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        e_ms = t0.elapsed_time(t1)
+        te = torch.tensor([e_ms], dtype=torch.float64, device="cuda")
+        if world > 1:
+            torch.distributed.all_reduce(te, op=torch.distributed.ReduceOp.MAX)
+        e_ms = float(te.item())
+        e2e = {"value": n * world * args.steps / (e_ms / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": int(S_host.numel() * 8),
+               "d2h_bytes_per_step": int(2 * n * 8 + 8)}
+
+    # roofline of the dominant kernel
+    kern = {k: v for k, v in prof.items() if v[1] > 0}
+    top = max(kern, key=lambda k: kern[k][0])
+    ms_top, launches_top = kern[top]
+    sample = spins[: min(256, n)]
+    if top == "pair_sandwich":
+        f_cfg = flops.pair_flops_batch(L, L, D, Dc, sample, J2) / len(sample)
+    elif top == "row_sandwich":
+        f_cfg = flops.row_flops_batch(L, L, D, Dc, sample) / len(sample)
+    else:
+        f_cfg = None
+    roofline = None
+    if f_cfg is not None:
+        flops_per_launch = f_cfg * n * args.steps / launches_top
+        achieved = flops_per_launch / (ms_top / launches_top / 1e3) / 1e12
+        roofline = {"bound": "alu", "kernel": top, "achieved": achieved, "peak": FP32_SIMT_TFLOPS,
+                    "unit": "TFLOP/s", "frac": achieved / FP32_SIMT_TFLOPS, "traffic": None,
+                    "peak_source": "FP32 SIMT: 152 SMs x 128 lanes x 2 flop x 2070 MHz (derived, nominal)",
+                    "flops_per_config": f_cfg}
+    share = {k: round(v[0] / sum(x[0] for x in kern.values()), 4) for k, v in kern.items()}
+    launches = sum(v[1] for v in kern.values())
+    value = n * world * args.steps / (total_ms / 1e3)
+    res = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if args.prec == "fp32" else "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "lattice": f"{L}x{L}", "D": D, "Dc": Dc, "J2_over_J1": J2,
+                   "configs_per_step_per_gpu": n, "precision_path": f"plain {args.prec.upper()} SIMT",
+                   "sampling": "uniform random Sz=0 configurations",
+                   "l2": "working set per step (environments, Delta) is tens of GB, far above L2",
+                   "parallelism": f"dp{world} (independent configurations)"},
+        "step_ms": {"p50": statistics.median(per_step), "p99": float(np.percentile(per_step, 99)),
+                    "max": max(per_step)},
+        "kernel_share": share, "gpu_launches": launches, "roofline": roofline, "clocks": clocks, "e2e": e2e,
+        "energy_per_site": out["energy_per_site"],
+    }
+    return res
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return None
+    w = inputs.WORKLOADS[args.workload]
+    rate = None
+    t0 = time.perf_counter()
+    samples = []
+    import multiprocessing as mp  # noqa: F401
+    for _ in range(max(1, args.warmup and 0) + args.steps):
+        c = cpu_oracle_rate(args.workload, args.cpu_seconds)
+        samples.append(c)
+    rate = statistics.median([c["value"] for c in samples])
+    cb = dict(samples[-1])
+    cb["value"] = rate
+    wall = time.perf_counter() - t0
+    return {
+        "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": wall * 1e3 / max(1, args.steps), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+        "config": {"workload": args.workload, "lattice": f"{w['L']}x{w['L']}", "D": w["D"], "Dc": w["Dc"],
+                   "J2_over_J1": w["J2"], "sampling": "uniform random Sz=0 configurations"},
+        "cpu_baseline": cb,
+        "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        res = run_reference(args, rank)
+        if res is not None:
+            print(json.dumps(res), flush=True)
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        # the oracle pool is spawned before any GPU work
+        cpu = cpu_oracle_rate(args.workload, args.cpu_seconds)
+    res = run_ours(args, rank, world, local_rank)
+    if rank == 0:
+        res["cpu_baseline"] = cpu
+        print(json.dumps(res), flush=True)
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

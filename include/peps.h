@@ -130,6 +130,16 @@ peps_status peps_gradient(peps_ctx* ctx, const uint64_t* S_dev, int n, double* e
 peps_status peps_mc_sweep(peps_ctx* ctx, uint64_t* S_dev, int n, int nsweeps, uint64_t seed, uint64_t chain0,
                           uint64_t sweep0, int64_t* accepted_dev);
 
+/* Per-kernel timing of this context's launches: when enabled, CUDA events
+ * are recorded on the context's stream around every kernel the library
+ * launches.  peps_profile_read synchronises the stream and returns, per
+ * kernel id (0 boundary sweeps, 1 single-row sandwiches, 2 two-row
+ * sandwiches, 3 E_loc/status finalisation, 4 gradient sums, 5 energy sum,
+ * 6 gradient finalisation, 7 Metropolis sweeps), the summed milliseconds
+ * and the number of launches since the last reset; reset clears them. */
+peps_status peps_profile_enable(peps_ctx* ctx, int on);
+peps_status peps_profile_read(peps_ctx* ctx, double* ms /* [8] */, long long* launches /* [8] */, int reset);
+
 /* Waits for the context's stream. */
 peps_status peps_synchronize(peps_ctx* ctx);
 

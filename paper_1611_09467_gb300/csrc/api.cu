@@ -103,7 +103,35 @@ struct peps_ctx {
   DevBuf A, triv_mps, triv_t1, triv_t2, bd;
   DevBuf env, small, O, scratch, gsum;
   int chunk = 0;  // configurations per pass
+  // profiling: event pairs per kernel id
+  bool prof = false;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev;
+  double ms[8] = {0};
+  long long launches[8] = {0};
 };
+
+namespace {
+// Brackets one launch with events when profiling is on; counts launches always.
+struct Prof {
+  peps_ctx* c;
+  int id;
+  cudaEvent_t a = nullptr, b = nullptr;
+  Prof(peps_ctx* c_, int id_) : c(c_), id(id_) {
+    c->launches[id] += 1;
+    if (c->prof) {
+      cudaEventCreate(&a);
+      cudaEventCreate(&b);
+      cudaEventRecord(a, c->stream);
+    }
+  }
+  ~Prof() {
+    if (c->prof) {
+      cudaEventRecord(b, c->stream);
+      c->ev.push_back({id, {a, b}});
+    }
+  }
+};
+}  // namespace
 
 namespace {
 
@@ -233,20 +261,28 @@ peps_status evaluate_chunk(peps_ctx* c, const uint64_t* S, int n, bool need_env_
   PEPS_CUDA(cudaMemsetAsync(sm.flags, 0, (size_t)n * sizeof(int), c->stream));
   const int dirs = need_env_l ? 2 : 1;
   int grid = std::min(n * dirs, std::min(c->nslots, max_blocks_boundary<R>(c->g)));
-  PEPS_CUDA(launch_boundary<R>(a, dirs, std::max(grid, 1), c->stream));
+  {
+    Prof pf(c, 0);
+    PEPS_CUDA(launch_boundary<R>(a, dirs, std::max(grid, 1), c->stream));
+  }
   if (need_env_l) {
     grid = std::min(n * c->g.Ly, c->nslots);
+    Prof pf(c, 1);
     PEPS_CUDA(launch_row<R>(a, std::max(grid, 1), c->stream));
   }
   if (need_pairs && c->g.Ly > 1) {
     grid = std::min(n * (c->g.Ly - 1), c->nslots);
+    Prof pf(c, 2);
     PEPS_CUDA(launch_pair<R>(a, std::max(grid, 1), c->stream));
   } else {
     PEPS_CUDA(cudaMemsetAsync(sm.eloc_v, 0, (size_t)n * c->g.Ly * sizeof(double), c->stream));
   }
   if (!need_env_l) PEPS_CUDA(cudaMemsetAsync(sm.eloc_h, 0, (size_t)n * c->g.Ly * sizeof(double), c->stream));
-  PEPS_CUDA(launch_finalize(c->g, S, n, sm.eloc_h, sm.eloc_v, sm.flags, sm.eloc, sm.status, need_env_l ? 1 : 0,
-                            c->stream));
+  {
+    Prof pf(c, 3);
+    PEPS_CUDA(launch_finalize(c->g, S, n, sm.eloc_h, sm.eloc_v, sm.flags, sm.eloc, sm.status, need_env_l ? 1 : 0,
+                              c->stream));
+  }
   return PEPS_OK;
 }
 
@@ -312,14 +348,23 @@ peps_status gradient_impl(peps_ctx* c, const uint64_t* S, int n, double* e_site,
     ga.status = sm.status;
     ga.sumO = sumO;
     ga.sumEO = sumEO;
-    PEPS_CUDA(launch_grad_accum<R>(ga, (const R*)c->O.p, c->stream));
-    PEPS_CUDA(launch_sum_eloc(sm.eloc, sm.status, m, sums, c->stream));
+    {
+      Prof pf(c, 4);
+      PEPS_CUDA(launch_grad_accum<R>(ga, (const R*)c->O.p, c->stream));
+    }
+    {
+      Prof pf(c, 5);
+      PEPS_CUDA(launch_sum_eloc(sm.eloc, sm.status, m, sums, c->stream));
+    }
     if (logabs) PEPS_CUDA(cudaMemcpyAsync(logabs + c0, sm.logabs, m * 8, cudaMemcpyDeviceToDevice, c->stream));
     if (sign) PEPS_CUDA(cudaMemcpyAsync(sign + c0, sm.sign, m, cudaMemcpyDeviceToDevice, c->stream));
     if (eloc) PEPS_CUDA(cudaMemcpyAsync(eloc + c0, sm.eloc, m * 8, cudaMemcpyDeviceToDevice, c->stream));
     if (status) PEPS_CUDA(cudaMemcpyAsync(status + c0, sm.status, m * 4, cudaMemcpyDeviceToDevice, c->stream));
   }
-  PEPS_CUDA(launch_grad_finalize((int)total, 0, sums, sumO, sumEO, grad, cov, c->stream));
+  {
+    Prof pf(c, 6);
+    PEPS_CUDA(launch_grad_finalize((int)total, 0, sums, sumO, sumEO, grad, cov, c->stream));
+  }
   double h[2] = {0, 0};
   PEPS_CUDA(cudaMemcpyAsync(h, sums, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
   PEPS_CUDA(cudaStreamSynchronize(c->stream));
@@ -338,6 +383,7 @@ peps_status mc_impl(peps_ctx* c, uint64_t* S, int n, int nsweeps, uint64_t seed,
   sm.carve(c->small.p, c->chunk, c->g.Ly);
   KArgs<R> a = make_args<R>(c, S, n, sm);
   const int grid = std::min(n, std::min(c->nslots, max_blocks_mc<R>(c->g)));
+  Prof pf(c, 7);
   PEPS_CUDA(launch_mc<R>(a, S, nsweeps, seed, chain0, sweep0, (long long*)accepted, std::max(grid, 1), c->stream));
   return PEPS_OK;
 }
@@ -421,6 +467,10 @@ peps_status peps_destroy(peps_ctx* c) {
   if (!c) return PEPS_OK;
   if (c->stream) cudaStreamSynchronize(c->stream);
   else cudaDeviceSynchronize();
+  for (auto& e : c->ev) {
+    cudaEventDestroy(e.second.first);
+    cudaEventDestroy(e.second.second);
+  }
   DevBuf* bufs[] = {&c->A, &c->triv_mps, &c->triv_t1, &c->triv_t2, &c->bd, &c->env, &c->small, &c->O, &c->scratch, &c->gsum};
   for (DevBuf* b : bufs) b->release();
   delete c;
@@ -474,6 +524,34 @@ peps_status peps_mc_sweep(peps_ctx* c, uint64_t* S, int n, int nsweeps, uint64_t
   g_err.clear();
   if (c->elem == 8) return mc_impl<double>(c, S, n, nsweeps, seed, chain0, sweep0, accepted);
   return mc_impl<float>(c, S, n, nsweeps, seed, chain0, sweep0, accepted);
+}
+
+peps_status peps_profile_enable(peps_ctx* c, int on) {
+  if (!c) return fail(PEPS_EINVAL, "null context");
+  c->prof = on != 0;
+  return PEPS_OK;
+}
+
+peps_status peps_profile_read(peps_ctx* c, double* ms, long long* launches, int reset) {
+  if (!c) return fail(PEPS_EINVAL, "null context");
+  PEPS_CUDA(cudaStreamSynchronize(c->stream));
+  for (auto& e : c->ev) {
+    float t = 0.f;
+    cudaEventElapsedTime(&t, e.second.first, e.second.second);
+    c->ms[e.first] += t;
+    cudaEventDestroy(e.second.first);
+    cudaEventDestroy(e.second.second);
+  }
+  c->ev.clear();
+  for (int i = 0; i < 8; ++i) {
+    if (ms) ms[i] = c->ms[i];
+    if (launches) launches[i] = c->launches[i];
+    if (reset) {
+      c->ms[i] = 0;
+      c->launches[i] = 0;
+    }
+  }
+  return PEPS_OK;
 }
 
 peps_status peps_synchronize(peps_ctx* c) {

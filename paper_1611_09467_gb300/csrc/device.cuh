@@ -54,64 +54,116 @@ __device__ R block_sum(R v, R* red) {
 }
 
 // ------------------------------------------------------------- CTA GEMM
-// Each thread owns 4x4 output tiles; operands are read through the index
-// maps of the descriptor (see contract.cuh).  No barrier inside: callers
-// synchronise between dependent steps.
-template <typename R>
-__device__ void cta_gemm(const GemmDesc& g, const R* __restrict__ A, const R* __restrict__ B,
-                         R* __restrict__ C, bool accumulate) {
-  const int tm = (g.M + 3) >> 2, tn = (g.N + 3) >> 2;
-  const int per_batch = tm * tn;
-  const int total = per_batch * g.nb;
-  const int kn2 = g.ak.n2;
-  const int k1n = g.K / kn2;
-  for (int t = threadIdx.x; t < total; t += blockDim.x) {
-    const int bt = t / per_batch, tt = t - bt * per_batch;
-    const int i0 = (tt / tn) * 4, j0 = (tt % tn) * 4;
+// Shared-memory tiled GEMM over the index maps of a descriptor (see
+// contract.cuh).  Per output tile (TM x TN) the K range is walked in chunks
+// of 16: the A and B chunks are gathered from global memory through the
+// offset tables into shared memory, then every thread accumulates an
+// MT x NT micro-tile in registers.  The CTA tile shape follows N (the
+// contraction steps have N in {16, 32, 64, 128, 256+}).  Shared memory:
+// kGemmSmemReals reals + kGemmSmemInts ints supplied by the caller.
+constexpr int kGemmTK = 16;
+constexpr int kMaxK = 1024;
+constexpr int kGemmSmemReals = kGemmTK * (512 + 16);
+constexpr int kGemmSmemInts = 2 * kMaxK + 2 * 512 + 2 * 256;
+
+template <typename R, int TM, int TN, int MT, int NT>
+__device__ __noinline__ void gemm_tiles(const GemmDesc& g, const R* __restrict__ A, const R* __restrict__ B,
+                                        R* __restrict__ C, bool accumulate, R* sm, int* ism) {
+  constexpr int TK = kGemmTK;
+  constexpr int GX = TN / NT, GY = TM / MT;
+  static_assert(GX * GY == kThreads, "thread grid must cover the CTA");
+  R* As = sm;                  // [TK][TM]
+  R* Bs = sm + TK * TM;        // [TK][TN]
+  int* ktA = ism;              // [K]
+  int* ktB = ism + kMaxK;      // [K]
+  int* rA = ism + 2 * kMaxK;   // [TM]
+  int* rC = rA + TM;           // [TM]
+  int* cB = rC + TM;           // [TN]
+  int* cC = cB + TN;           // [TN]
+  const int tid = threadIdx.x;
+  const int tx = tid % GX, ty = tid / GX;
+  __syncthreads();
+  for (int k = tid; k < g.K; k += blockDim.x) {
+    const int k1 = k / g.ak.n2, k2 = k - k1 * g.ak.n2;
+    ktA[k] = k1 * g.ak.s1 + k2 * g.ak.s2;
+    ktB[k] = k1 * g.bk.s1 + k2 * g.bk.s2;
+  }
+  const int tiles_m = (g.M + TM - 1) / TM, tiles_n = (g.N + TN - 1) / TN;
+  for (int bt = 0; bt < g.nb; ++bt) {
     const R* Ab = A + (size_t)bt * g.sa;
     const R* Bb = B + (size_t)bt * g.sb;
     R* Cb = C + (size_t)bt * g.sc;
-    int ao[4], cm[4], bo[4], cn[4];
+    for (int tmi = 0; tmi < tiles_m; ++tmi)
+      for (int tni = 0; tni < tiles_n; ++tni) {
+        const int i0 = tmi * TM, j0 = tni * TN;
+        __syncthreads();
+        for (int e = tid; e < TM; e += blockDim.x) {
+          const int i = min(i0 + e, g.M - 1);
+          rA[e] = ixoff(g.am, i);
+          rC[e] = ixoff(g.cm, i);
+        }
+        for (int e = tid; e < TN; e += blockDim.x) {
+          const int j = min(j0 + e, g.N - 1);
+          cB[e] = ixoff(g.bn, j);
+          cC[e] = ixoff(g.cn, j);
+        }
+        R acc[MT][NT];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int i = min(i0 + q, g.M - 1), j = min(j0 + q, g.N - 1);
-      ao[q] = ixoff(g.am, i);
-      cm[q] = ixoff(g.cm, i);
-      bo[q] = ixoff(g.bn, j);
-      cn[q] = ixoff(g.cn, j);
-    }
-    R acc[4][4];
+        for (int m = 0; m < MT; ++m)
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+          for (int n = 0; n < NT; ++n) acc[m][n] = R(0);
+        for (int k0 = 0; k0 < g.K; k0 += TK) {
+          __syncthreads();
+          for (int e = tid; e < TM * TK; e += kThreads) {
+            const int i = e % TM, kk = e / TM, k = k0 + kk;
+            As[kk * TM + i] = k < g.K ? Ab[rA[i] + ktA[k]] : R(0);
+          }
+          for (int e = tid; e < TN * TK; e += kThreads) {
+            const int j = e % TN, kk = e / TN, k = k0 + kk;
+            Bs[kk * TN + j] = k < g.K ? Bb[ktB[k] + cB[j]] : R(0);
+          }
+          __syncthreads();
 #pragma unroll
-      for (int b = 0; b < 4; ++b) acc[a][b] = R(0);
-    for (int k1 = 0; k1 < k1n; ++k1) {
-      const R* pa = Ab + k1 * g.ak.s1;
-      const R* pb = Bb + k1 * g.bk.s1;
-      for (int k2 = 0; k2 < kn2; ++k2) {
-        R av[4], bv[4];
+          for (int kk = 0; kk < TK; ++kk) {
+            R a[MT], b[NT];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          av[q] = pa[ao[q] + k2 * g.ak.s2];
-          bv[q] = pb[bo[q] + k2 * g.bk.s2];
+            for (int m = 0; m < MT; ++m) a[m] = As[kk * TM + ty * MT + m];
+#pragma unroll
+            for (int n = 0; n < NT; ++n) b[n] = Bs[kk * TN + tx * NT + n];
+#pragma unroll
+            for (int m = 0; m < MT; ++m)
+#pragma unroll
+              for (int n = 0; n < NT; ++n) acc[m][n] = fma(a[m], b[n], acc[m][n]);
+          }
         }
 #pragma unroll
-        for (int a = 0; a < 4; ++a)
+        for (int m = 0; m < MT; ++m) {
+          const int i = ty * MT + m;
+          if (i0 + i >= g.M) break;
 #pragma unroll
-          for (int b = 0; b < 4; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+          for (int n = 0; n < NT; ++n) {
+            const int j = tx * NT + n;
+            if (j0 + j >= g.N) break;
+            R* p = Cb + rC[i] + cC[j];
+            *p = accumulate ? *p + acc[m][n] : acc[m][n];
+          }
+        }
       }
-    }
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      if (i0 + a >= g.M) break;
-#pragma unroll
-      for (int b = 0; b < 4; ++b) {
-        if (j0 + b >= g.N) break;
-        R* p = Cb + cm[a] + cn[b];
-        *p = accumulate ? *p + acc[a][b] : acc[a][b];
-      }
-    }
   }
+  __syncthreads();
+}
+
+// C (+)= A B for a descriptor; the whole CTA takes part and the call ends
+// with a barrier.  `sm`/`ism` point to the GEMM's shared-memory scratch.
+template <typename R>
+__device__ void cta_gemm(const GemmDesc& g, const R* __restrict__ A, const R* __restrict__ B, R* __restrict__ C,
+                         bool accumulate, R* sm, int* ism) {
+  if (g.N >= 256 && g.M <= 32) gemm_tiles<R, 16, 256, 4, 4>(g, A, B, C, accumulate, sm, ism);
+  else if (g.N >= 128) gemm_tiles<R, 64, 128, 4, 8>(g, A, B, C, accumulate, sm, ism);
+  else if (g.N >= 64 && g.M >= 128) gemm_tiles<R, 128, 64, 8, 4>(g, A, B, C, accumulate, sm, ism);
+  else if (g.N >= 48) gemm_tiles<R, 64, 64, 4, 4>(g, A, B, C, accumulate, sm, ism);
+  else if (g.N >= 24) gemm_tiles<R, 256, 32, 8, 4>(g, A, B, C, accumulate, sm, ism);
+  else gemm_tiles<R, 512, 16, 8, 4>(g, A, B, C, accumulate, sm, ism);
 }
 
 // ------------------------------------------------- contraction programs
@@ -163,14 +215,13 @@ PEPS_HD GemmDesc op_desc(int op, int s, int D, int Dc) {
 // Runs one contraction program with the whole CTA; ends with a barrier.
 template <typename R>
 __device__ void run_op(int op, int D, int Dc, const R* in0, const R* in1, const R* in2, const R* in3,
-                       const R* in4, R* out, R* t0, R* t1) {
+                       const R* in4, R* out, R* t0, R* t1, R* sm, int* ism) {
   const int ns = op_nsteps(op);
   for (int s = 0; s < ns; ++s) {
     const Step st = op_step_bufs(op, s);
     const GemmDesc g = op_desc(op, st.s, D, Dc);
     const R* bufs[8] = {in0, in1, in2, in3, in4, t0, t1, out};
-    cta_gemm<R>(g, bufs[st.a], bufs[st.b], const_cast<R*>(bufs[st.c]), false);
-    __syncthreads();
+    cta_gemm<R>(g, bufs[st.a], bufs[st.b], const_cast<R*>(bufs[st.c]), false, sm, ism);
   }
 }
 
@@ -197,6 +248,9 @@ struct TruncWork {
   R* Ub;      // Qmax x Kmax
   R* Uk;      // Pmax x Kmax
   R* red;     // >= 64 (shared)
+  R* wv;      // >= 256 (shared): reflector products
+  R* gsm;     // GEMM shared scratch (may alias Wm: used only after the reflectors are dead)
+  int* gism;
   int Qmax;
 };
 
@@ -227,6 +281,11 @@ __device__ __forceinline__ void householder(R alpha, R ss, R& tau, R& scale, R& 
   }
 }
 
+__device__ __forceinline__ double sturm_div(double a, double b) { return a / b; }
+__device__ __forceinline__ float sturm_div(float a, float b) { return __fdividef(a, b); }
+
+// Number of eigenvalues below x of the zero-diagonal symmetric tridiagonal
+// with squared off-diagonals t2 (pivots of the LDL^T factorisation of T - x).
 template <typename R>
 __device__ int sturm_count(const R* t2, int n2, R x, R pivmin) {
   int cnt = 0;
@@ -234,7 +293,7 @@ __device__ int sturm_count(const R* t2, int n2, R x, R pivmin) {
   if (fabs(q) < pivmin) q = -pivmin;
   if (q < R(0)) ++cnt;
   for (int i = 1; i < n2; ++i) {
-    q = -x - t2[i - 1] / q;
+    q = -x - sturm_div(t2[i - 1], q);
     if (fabs(q) < pivmin) q = -pivmin;
     if (q < R(0)) ++cnt;
   }
@@ -281,8 +340,10 @@ __device__ void inverse_iteration(const R* t, int n2, R lam, R pivtiny, R* ws, R
       }
     }
   }
-  for (int i = 0; i < n2; ++i)
+  for (int i = 0; i < n2; ++i) {
     if (fabs(dd[i]) < pivtiny) dd[i] = dd[i] < R(0) ? -pivtiny : pivtiny;
+    dd[i] = R(1) / dd[i];   // stored as reciprocals for the solves
+  }
   // start vector
   unsigned h = seed * 2654435761u + 12345u;
   for (int i = 0; i < n2; ++i) {
@@ -299,9 +360,9 @@ __device__ void inverse_iteration(const R* t, int n2, R lam, R pivtiny, R* ws, R
         b[i + 1] = tmp - mult[i] * b[i];
       }
     }
-    b[n2 - 1] /= dd[n2 - 1];
-    if (n2 >= 2) b[n2 - 2] = (b[n2 - 2] - du[n2 - 2] * b[n2 - 1]) / dd[n2 - 2];
-    for (int i = n2 - 3; i >= 0; --i) b[i] = (b[i] - du[i] * b[i + 1] - du2[i] * b[i + 2]) / dd[i];
+    b[n2 - 1] *= dd[n2 - 1];
+    if (n2 >= 2) b[n2 - 2] = (b[n2 - 2] - du[n2 - 2] * b[n2 - 1]) * dd[n2 - 2];
+    for (int i = n2 - 3; i >= 0; --i) b[i] = (b[i] - du[i] * b[i + 1] - du2[i] * b[i + 2]) * dd[i];
     R mx = R(0);
     for (int i = 0; i < n2; ++i) mx = fmax(mx, fabs(b[i]));
     if (!(mx > R(0))) mx = R(1);
@@ -349,6 +410,10 @@ __device__ void cta_topk_left(const R* X, int m, int n, int K, TruncWork<R>& w, 
   R* tauR = w.tau + w.Qmax;
   R* red = w.red;
   // ---------------- bidiagonalisation: W = Q_L B Q_R^T, B upper bidiagonal
+  // Each reflector: one warp forms it, then the whole CTA computes the
+  // reflector-matrix products (thread groups per column / row) and applies
+  // the rank-1 update.
+  R* wv = w.wv;
   for (int j = 0; j < Q; ++j) {
     if (warp == 0) {
       R ss = R(0);
@@ -369,15 +434,31 @@ __device__ void cta_topk_left(const R* X, int m, int n, int K, TruncWork<R>& w, 
     __syncthreads();
     {
       const R tau = red[0], scale = red[1];
-      for (int i = j + 1 + tid; i < P; i += blockDim.x) W[i * ld + j] *= scale;
-      __syncthreads();
+      const int ncol = Q - j - 1;
       if (tau != R(0)) {
-        for (int c = j + 1 + warp; c < Q; c += kWarps) {
-          R s = lane == 0 ? W[j * ld + c] : R(0);
-          for (int i = j + 1 + lane; i < P; i += 32) s += W[i * ld + j] * W[i * ld + c];
-          s = warp_sum(s) * tau;
-          if (lane == 0) W[j * ld + c] -= s;
-          for (int i = j + 1 + lane; i < P; i += 32) W[i * ld + c] -= s * W[i * ld + j];
+        for (int i = j + 1 + tid; i < P; i += blockDim.x) W[i * ld + j] *= scale;
+        __syncthreads();
+      }
+      if (tau != R(0) && ncol > 0) {
+        // wv[c] = tau * (W[j][c] + sum_{i>j} v_i W[i][c])
+        int tpc = kThreads / ncol;
+        tpc = tpc >= 32 ? 32 : tpc >= 16 ? 16 : tpc >= 8 ? 8 : tpc >= 4 ? 4 : tpc >= 2 ? 2 : 1;
+        const int cpr = kThreads / tpc;
+        for (int cb = 0; cb < ncol; cb += cpr) {
+          const int cl = cb + tid / tpc, gl = tid % tpc;
+          const bool act = cl < ncol;
+          const int c = j + 1 + (act ? cl : 0);
+          R sacc = (gl == 0) ? W[j * ld + c] : R(0);
+          for (int i = j + 1 + gl; i < P; i += tpc) sacc += W[i * ld + j] * W[i * ld + c];
+          sacc = warp_sum(sacc, tpc);
+          if (act && gl == 0) wv[c] = sacc * tau;
+        }
+        __syncthreads();
+        const int rows = P - j;
+        for (int e = tid; e < rows * ncol; e += blockDim.x) {
+          const int ii = e / ncol, c = j + 1 + e % ncol, i = j + ii;
+          const R v = ii == 0 ? R(1) : W[i * ld + j];
+          W[i * ld + c] -= wv[c] * v;
         }
       }
       __syncthreads();
@@ -401,15 +482,30 @@ __device__ void cta_topk_left(const R* X, int m, int n, int K, TruncWork<R>& w, 
       }
       __syncthreads();
       const R tau = red[2], scale = red[3];
-      for (int c = j + 2 + tid; c < Q; c += blockDim.x) W[j * ld + c] *= scale;
-      __syncthreads();
+      const int nrow = P - j - 1, ncol = Q - j - 1;
       if (tau != R(0)) {
-        for (int i = j + 1 + warp; i < P; i += kWarps) {
-          R s = lane == 0 ? W[i * ld + j + 1] : R(0);
-          for (int c = j + 2 + lane; c < Q; c += 32) s += W[i * ld + c] * W[j * ld + c];
-          s = warp_sum(s) * tau;
-          if (lane == 0) W[i * ld + j + 1] -= s;
-          for (int c = j + 2 + lane; c < Q; c += 32) W[i * ld + c] -= s * W[j * ld + c];
+        for (int c = j + 2 + tid; c < Q; c += blockDim.x) W[j * ld + c] *= scale;
+        __syncthreads();
+      }
+      if (tau != R(0) && nrow > 0) {
+        // wv[i] = tau * (W[i][j+1] + sum_{c>j+1} W[i][c] v'_c)
+        int tpc = kThreads / nrow;
+        tpc = tpc >= 32 ? 32 : tpc >= 16 ? 16 : tpc >= 8 ? 8 : tpc >= 4 ? 4 : tpc >= 2 ? 2 : 1;
+        const int rpr = kThreads / tpc;
+        for (int rb = 0; rb < nrow; rb += rpr) {
+          const int rl = rb + tid / tpc, gl = tid % tpc;
+          const bool act = rl < nrow;
+          const int i = j + 1 + (act ? rl : 0);
+          R sacc = (gl == 0) ? W[i * ld + j + 1] : R(0);
+          for (int c = j + 2 + gl; c < Q; c += tpc) sacc += W[i * ld + c] * W[j * ld + c];
+          sacc = warp_sum(sacc, tpc);
+          if (act && gl == 0) wv[i] = sacc * tau;
+        }
+        __syncthreads();
+        for (int e = tid; e < nrow * ncol; e += blockDim.x) {
+          const int i = j + 1 + e / ncol, cc = e % ncol, c = j + 1 + cc;
+          const R v = cc == 0 ? R(1) : W[j * ld + c];
+          W[i * ld + c] -= wv[i] * v;
         }
       }
       __syncthreads();
@@ -560,8 +656,7 @@ __device__ void cta_topk_left(const R* X, int m, int n, int K, TruncWork<R>& w, 
   }
   // C' = U_K^T X
   GemmDesc g = gemm(K, n, m, ix1(1), kx(m, 0, K), kx(m, 0, n), ix1(1), co_r, co_c);
-  cta_gemm<R>(g, Uk, X, Cout, false);
-  __syncthreads();
+  cta_gemm<R>(g, Uk, X, Cout, false, w.gsm, w.gism);
 }
 
 }  // namespace peps

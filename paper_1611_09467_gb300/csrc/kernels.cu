@@ -17,6 +17,7 @@
 //
 // Kernels are persistent over work items (grid-stride), so the per-CTA
 // scratch slots bound the workspace.
+#include <algorithm>
 #include <cstdio>
 
 #include "device.cuh"
@@ -48,6 +49,29 @@ __device__ __forceinline__ TDims tdims(const Geometry& g, int row, int col) {
 size_t wm_smem_bytes(const Geometry& g, size_t elem) {
   const size_t P = (size_t)g.Dc * g.D;
   return P * (P + 1) * elem;
+}
+
+// Dynamic shared memory of a kernel: a region of reals (the truncation
+// matrix when it lives in shared memory, or the GEMM tiles; the two are never
+// live together) followed by the GEMM offset tables.
+size_t dyn_smem_bytes(const Geometry& g, size_t elem, bool with_wm) {
+  size_t reals = (size_t)kGemmSmemReals * elem;
+  if (with_wm) reals = std::max(reals, wm_smem_bytes(g, elem));
+  reals = (reals + 15) / 16 * 16;
+  return reals + (size_t)kGemmSmemInts * sizeof(int);
+}
+
+template <typename R>
+__device__ __forceinline__ void smem_split(unsigned char* raw, const Geometry& g, bool with_wm, R*& reals, int*& ints) {
+  size_t rb = (size_t)kGemmSmemReals * sizeof(R);
+  if (with_wm) {
+    const size_t P = (size_t)g.Dc * g.D;
+    const size_t wb = P * (P + 1) * sizeof(R);
+    rb = rb > wb ? rb : wb;
+  }
+  rb = (rb + 15) / 16 * 16;
+  reals = reinterpret_cast<R*>(raw);
+  ints = reinterpret_cast<int*>(raw + rb);
 }
 
 static size_t zip_elems(const Geometry& g, bool wm_in_smem) {
@@ -93,11 +117,14 @@ struct ZipBufs {
   R* C1;
   R* Y;
   R* X;
+  double* dred;   // >= kWarps doubles of shared memory
+  R* gsm;         // GEMM shared scratch
+  int* gism;
   TruncWork<R> tw;
 };
 
 template <typename R>
-__device__ R absorb_row(const KArgs<R>& a, const R* Min, R* Mout, int row, int dir, bool lr, const int* bdin,
+__device__ double absorb_row(const KArgs<R>& a, const R* Min, R* Mout, int row, int dir, bool lr, const int* bdin,
                         const uint64_t* sp, ZipBufs<R>& zb, R* red) {
   const Geometry& g = a.g;
   const int D = g.D, Dc = g.Dc, Lx = g.Lx;
@@ -121,10 +148,8 @@ __device__ R absorb_row(const KArgs<R>& a, const R* Min, R* Mout, int row, int d
       z.l = td.l; z.r = td.r;
       z.o = dir == 0 ? td.d : td.u;
       const R* T = tptr(a, row * Lx + c, spin_of(sp, row * Lx + c));
-      cta_gemm<R>(zip_lr_step(0, z, D, Dc, sl, sr, si, so), Cc, Min + (size_t)c * envT, zb.Y, false);
-      __syncthreads();
-      cta_gemm<R>(zip_lr_step(1, z, D, Dc, sl, sr, si, so), zb.Y, T, zb.X, false);
-      __syncthreads();
+      cta_gemm<R>(zip_lr_step(0, z, D, Dc, sl, sr, si, so), Cc, Min + (size_t)c * envT, zb.Y, false, zb.gsm, zb.gism);
+      cta_gemm<R>(zip_lr_step(1, z, D, Dc, sl, sr, si, so), zb.Y, T, zb.X, false, zb.gsm, zb.gism);
       const int m = z.k * z.o, n = z.b * z.r;
       if (c < Lx - 1) {
         const int K = min(Dc, min(m, n));
@@ -150,10 +175,8 @@ __device__ R absorb_row(const KArgs<R>& a, const R* Min, R* Mout, int row, int d
       z.l = td.l; z.r = td.r;
       z.o = dir == 0 ? td.d : td.u;
       const R* T = tptr(a, row * Lx + c, spin_of(sp, row * Lx + c));
-      cta_gemm<R>(zip_rl_step(0, z, D, Dc, sl, sr, si, so), Min + (size_t)c * envT, Cc, zb.Y, false);
-      __syncthreads();
-      cta_gemm<R>(zip_rl_step(1, z, D, Dc, sl, sr, si, so), zb.Y, T, zb.X, false);
-      __syncthreads();
+      cta_gemm<R>(zip_rl_step(0, z, D, Dc, sl, sr, si, so), Min + (size_t)c * envT, Cc, zb.Y, false, zb.gsm, zb.gism);
+      cta_gemm<R>(zip_rl_step(1, z, D, Dc, sl, sr, si, so), zb.Y, T, zb.X, false, zb.gsm, zb.gism);
       const int m = z.o * z.k, n = z.a * z.l;
       if (c > 0) {
         const int K = min(Dc, min(m, n));
@@ -171,13 +194,14 @@ __device__ R absorb_row(const KArgs<R>& a, const R* Min, R* Mout, int row, int d
     }
     last = 0;
   }
-  R ss = R(0);
+  // the norm is accumulated in FP64 in every precision: ln n enters ln|psi| directly
+  double ss = 0.0;
   R* Ml = Mout + (size_t)last * envT;
-  for (int e = threadIdx.x; e < envT; e += blockDim.x) ss += Ml[e] * Ml[e];
-  ss = block_sum(ss, red);
-  const R nrm = dsqrt(ss);
-  if (nrm > R(0)) {
-    const R inv = R(1) / nrm;
+  for (int e = threadIdx.x; e < envT; e += blockDim.x) ss += (double)Ml[e] * (double)Ml[e];
+  ss = block_sum(ss, zb.dred);
+  const double nrm = sqrt(ss);
+  if (nrm > 0.0) {
+    const R inv = (R)(1.0 / nrm);
     for (int e = threadIdx.x; e < envT; e += blockDim.x) Ml[e] *= inv;
   }
   __syncthreads();
@@ -185,7 +209,14 @@ __device__ R absorb_row(const KArgs<R>& a, const R* Min, R* Mout, int row, int d
 }
 
 template <typename R>
-__device__ void carve_zip(const Geometry& g, R*& p, ZipBufs<R>& zb, R* wm_smem, R* red) {
+__device__ void carve_zip(const Geometry& g, R*& p, ZipBufs<R>& zb, R* wm_smem, R* red, double* dred, R* wv,
+                          R* gsm, int* gism) {
+  zb.dred = dred;
+  zb.gsm = gsm;
+  zb.gism = gism;
+  zb.tw.wv = wv;
+  zb.tw.gsm = gsm;
+  zb.tw.gism = gism;
   const size_t Dc = g.Dc, D = g.D, P = Dc * D;
   zb.C0 = p; p += Dc * Dc * D;
   zb.C1 = p; p += Dc * Dc * D;
@@ -223,7 +254,12 @@ __global__ void __launch_bounds__(kThreads) k_boundary(KArgs<R> a, int dirs) {
   const size_t envT = (size_t)Dc * D * Dc;
   R* p = a.scratch + (size_t)blockIdx.x * a.slot_elems;
   ZipBufs<R> zb;
-  carve_zip<R>(g, p, zb, a.smem_wm ? reinterpret_cast<R*>(smem_raw) : nullptr, red);
+  __shared__ double dred[kWarps];
+  __shared__ R wv[kMaxDcD];
+  R* gsm;
+  int* gism;
+  smem_split<R>(smem_raw, g, a.smem_wm != 0, gsm, gism);
+  carve_zip<R>(g, p, zb, a.smem_wm ? gsm : nullptr, red, dred, wv, gsm, gism);
   R* lastbuf = p;
   for (int i = threadIdx.x; i <= Lx; i += blockDim.x) ones[i] = 1;
   for (int item = blockIdx.x; item < a.n * dirs; item += gridDim.x) {
@@ -241,9 +277,9 @@ __global__ void __launch_bounds__(kThreads) k_boundary(KArgs<R> a, int dirs) {
       if (dir == 0) Mout = r <= Ly - 2 ? a.envU + ((size_t)cfg * Ly + r) * Lx * envT : lastbuf;
       else Mout = a.envL + ((size_t)cfg * Ly + r) * Lx * envT;
       const int* bdin = j == 0 ? ones : a.bd + ((size_t)dir * Ly + (j - 1)) * (Lx + 1);
-      const R nrm = absorb_row<R>(a, Min, Mout, r, dir, (j % 2) == 0, bdin, sp, zb, red);
-      if (!(nrm > R(0))) zero = true;
-      else ls += log((double)nrm);
+      const double nrm = absorb_row<R>(a, Min, Mout, r, dir, (j % 2) == 0, bdin, sp, zb, red);
+      if (!(nrm > 0.0)) zero = true;
+      else ls += log(nrm);
       Min = Mout;
     }
     if (dir == 0) {
@@ -290,11 +326,15 @@ __device__ R block_dot(const R* x, const R* y, int n, R* red) {
 // ----------------------------------------------------------------- k_row
 template <typename R>
 __global__ void __launch_bounds__(kThreads) k_row(KArgs<R> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ R red[64];
   __shared__ uint64_t sp[kMaxWords];
   const Geometry& g = a.g;
   const int Lx = g.Lx, Ly = g.Ly, Dc = g.Dc, D = g.D;
   const int envT = Dc * D * Dc, D4 = D * D * D * D;
+  R* gsm;
+  int* gism;
+  smem_split<R>(smem_raw, g, false, gsm, gism);
   R* p = a.scratch + (size_t)blockIdx.x * a.slot_elems;
   R* Gb = p; p += (size_t)(Lx + 1) * envT;
   R* F0 = p; p += envT;
@@ -315,7 +355,7 @@ __global__ void __launch_bounds__(kThreads) k_row(KArgs<R> a) {
     for (int c = Lx - 1; c >= 0; --c) {
       const int site = r * Lx + c;
       run_op<R>(OP_COL1_RIGHT, D, Dc, Gb + (size_t)(c + 1) * envT, Mu + (size_t)c * envT,
-                tptr(a, site, spin_of(sp, site)), Md + (size_t)c * envT, nullptr, Gb + (size_t)c * envT, t0, t1);
+                tptr(a, site, spin_of(sp, site)), Md + (size_t)c * envT, nullptr, Gb + (size_t)c * envT, t0, t1, gsm, gism);
     }
     const R W = Gb[0];
     const bool ok = W != R(0);
@@ -327,7 +367,7 @@ __global__ void __launch_bounds__(kThreads) k_row(KArgs<R> a) {
       const int s = spin_of(sp, site);
       if (a.O != nullptr) {
         run_op<R>(OP_SITE_ENV, D, Dc, F, Mu + (size_t)c * envT, Md + (size_t)c * envT,
-                  Gb + (size_t)(c + 1) * envT, nullptr, Bb, t0, t1);
+                  Gb + (size_t)(c + 1) * envT, nullptr, Bb, t0, t1, gsm, gism);
         R* Oo = a.O + ((size_t)cfg * g.N + site) * D4;
         const R inv = ok ? R(1) / W : R(0);
         for (int e = threadIdx.x; e < D4; e += blockDim.x) Oo[e] = Bb[e] * inv;
@@ -336,14 +376,14 @@ __global__ void __launch_bounds__(kThreads) k_row(KArgs<R> a) {
         const int s2 = spin_of(sp, site + 1);
         if (s != s2) {
           run_op<R>(OP_COL1_LEFT, D, Dc, F, Mu + (size_t)c * envT, tptr(a, site, s2), Md + (size_t)c * envT,
-                    nullptr, X1, t0, t1);
+                    nullptr, X1, t0, t1, gsm, gism);
           run_op<R>(OP_COL1_LEFT, D, Dc, X1, Mu + (size_t)(c + 1) * envT, tptr(a, site + 1, s),
-                    Md + (size_t)(c + 1) * envT, nullptr, X2, t0, t1);
+                    Md + (size_t)(c + 1) * envT, nullptr, X2, t0, t1, gsm, gism);
           const R wp = block_dot(X2, Gb + (size_t)(c + 2) * envT, envT, red);
           if (ok) eh += 0.5 * g.J1 * ((double)wp / (double)W);
         }
         run_op<R>(OP_COL1_LEFT, D, Dc, F, Mu + (size_t)c * envT, tptr(a, site, s), Md + (size_t)c * envT,
-                  nullptr, Fn, t0, t1);
+                  nullptr, Fn, t0, t1, gsm, gism);
         F = Fn;
         Fn = (Fn == F0) ? F1 : F0;
       }
@@ -359,11 +399,15 @@ __global__ void __launch_bounds__(kThreads) k_row(KArgs<R> a) {
 // ---------------------------------------------------------------- k_pair
 template <typename R>
 __global__ void __launch_bounds__(kThreads) k_pair(KArgs<R> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ R red[64];
   __shared__ uint64_t sp[kMaxWords];
   const Geometry& g = a.g;
   const int Lx = g.Lx, Ly = g.Ly, Dc = g.Dc, D = g.D;
   const int envT = Dc * D * Dc, envT2 = Dc * D * D * Dc;
+  R* gsm;
+  int* gism;
+  smem_split<R>(smem_raw, g, false, gsm, gism);
   R* p = a.scratch + (size_t)blockIdx.x * a.slot_elems;
   R* Hb = p; p += (size_t)(Lx + 1) * envT2;
   R* E0 = p; p += envT2;
@@ -385,7 +429,7 @@ __global__ void __launch_bounds__(kThreads) k_pair(KArgs<R> a) {
       const int s1 = r * Lx + c, s2 = (r + 1) * Lx + c;
       run_op<R>(OP_COL2_RIGHT, D, Dc, Hb + (size_t)(c + 1) * envT2, Mu + (size_t)c * envT,
                 tptr(a, s1, spin_of(sp, s1)), tptr(a, s2, spin_of(sp, s2)), Md + (size_t)c * envT,
-                Hb + (size_t)c * envT2, t0, t1);
+                Hb + (size_t)c * envT2, t0, t1, gsm, gism);
     }
     const R W = Hb[0];
     const bool ok = W != R(0);
@@ -398,7 +442,7 @@ __global__ void __launch_bounds__(kThreads) k_pair(KArgs<R> a) {
       const R* Muc = Mu + (size_t)c * envT;
       const R* Mdc = Md + (size_t)c * envT;
       if (a1 != a2) {  // vertical pair (r,c)-(r+1,c)
-        run_op<R>(OP_COL2_LEFT, D, Dc, E, Muc, tptr(a, i1, a2), tptr(a, i2, a1), Mdc, X1, t0, t1);
+        run_op<R>(OP_COL2_LEFT, D, Dc, E, Muc, tptr(a, i1, a2), tptr(a, i2, a1), Mdc, X1, t0, t1, gsm, gism);
         const R wp = block_dot(X1, Hb + (size_t)(c + 1) * envT2, envT2, red);
         if (ok) ev += 0.5 * g.J1 * ((double)wp / (double)W);
       }
@@ -408,20 +452,20 @@ __global__ void __launch_bounds__(kThreads) k_pair(KArgs<R> a) {
         const R* Mun = Mu + (size_t)(c + 1) * envT;
         const R* Mdn = Md + (size_t)(c + 1) * envT;
         if (a1 != b2) {  // diagonal (r,c)-(r+1,c+1)
-          run_op<R>(OP_COL2_LEFT, D, Dc, E, Muc, tptr(a, i1, b2), tptr(a, i2, a2), Mdc, X1, t0, t1);
-          run_op<R>(OP_COL2_LEFT, D, Dc, X1, Mun, tptr(a, j1, b1), tptr(a, j2, a1), Mdn, X2, t0, t1);
+          run_op<R>(OP_COL2_LEFT, D, Dc, E, Muc, tptr(a, i1, b2), tptr(a, i2, a2), Mdc, X1, t0, t1, gsm, gism);
+          run_op<R>(OP_COL2_LEFT, D, Dc, X1, Mun, tptr(a, j1, b1), tptr(a, j2, a1), Mdn, X2, t0, t1, gsm, gism);
           const R wp = block_dot(X2, Hb + (size_t)(c + 2) * envT2, envT2, red);
           if (ok) ev += 0.5 * g.J2 * ((double)wp / (double)W);
         }
         if (b1 != a2) {  // anti-diagonal (r,c+1)-(r+1,c)
-          run_op<R>(OP_COL2_LEFT, D, Dc, E, Muc, tptr(a, i1, a1), tptr(a, i2, b1), Mdc, X1, t0, t1);
-          run_op<R>(OP_COL2_LEFT, D, Dc, X1, Mun, tptr(a, j1, a2), tptr(a, j2, b2), Mdn, X2, t0, t1);
+          run_op<R>(OP_COL2_LEFT, D, Dc, E, Muc, tptr(a, i1, a1), tptr(a, i2, b1), Mdc, X1, t0, t1, gsm, gism);
+          run_op<R>(OP_COL2_LEFT, D, Dc, X1, Mun, tptr(a, j1, a2), tptr(a, j2, b2), Mdn, X2, t0, t1, gsm, gism);
           const R wp = block_dot(X2, Hb + (size_t)(c + 2) * envT2, envT2, red);
           if (ok) ev += 0.5 * g.J2 * ((double)wp / (double)W);
         }
       }
       if (c < Lx - 1) {
-        run_op<R>(OP_COL2_LEFT, D, Dc, E, Muc, tptr(a, i1, a1), tptr(a, i2, a2), Mdc, En, t0, t1);
+        run_op<R>(OP_COL2_LEFT, D, Dc, E, Muc, tptr(a, i1, a1), tptr(a, i2, a2), Mdc, En, t0, t1, gsm, gism);
         E = En;
         En = (En == E0) ? E1 : E0;
       }
@@ -572,7 +616,12 @@ __global__ void __launch_bounds__(kThreads) k_mc(KArgs<R> a, uint64_t* S, int ns
   Ubuf[0] = p; p += (size_t)Lx * envT;
   Ubuf[1] = p; p += (size_t)Lx * envT;
   ZipBufs<R> zb;
-  carve_zip<R>(g, p, zb, a.smem_wm ? reinterpret_cast<R*>(smem_raw) : nullptr, red);
+  __shared__ double dred[kWarps];
+  __shared__ R wv[kMaxDcD];
+  R* gsm;
+  int* gism;
+  smem_split<R>(smem_raw, g, a.smem_wm != 0, gsm, gism);
+  carve_zip<R>(g, p, zb, a.smem_wm ? gsm : nullptr, red, dred, wv, gsm, gism);
   R* Hb = p; p += (size_t)(Lx + 1) * envT2;
   R* Q[4];
   for (int q = 0; q < 4; ++q) { Q[q] = p; p += envT2; }
@@ -612,11 +661,11 @@ __global__ void __launch_bounds__(kThreads) k_mc(KArgs<R> a, uint64_t* S, int ns
             const int i1 = r * Lx + c;
             if (pass == 0)
               run_op<R>(OP_COL1_RIGHT, D, Dc, Hb + (size_t)(c + 1) * tsz, Mu + (size_t)c * envT,
-                        tptr(a, i1, spin_of(sp, i1)), Md + (size_t)c * envT, nullptr, Hb + (size_t)c * tsz, t0, t1);
+                        tptr(a, i1, spin_of(sp, i1)), Md + (size_t)c * envT, nullptr, Hb + (size_t)c * tsz, t0, t1, gsm, gism);
             else
               run_op<R>(OP_COL2_RIGHT, D, Dc, Hb + (size_t)(c + 1) * tsz, Mu + (size_t)c * envT,
                         tptr(a, i1, spin_of(sp, i1)), tptr(a, i1 + Lx, spin_of(sp, i1 + Lx)),
-                        Md + (size_t)c * envT, Hb + (size_t)c * tsz, t0, t1);
+                        Md + (size_t)c * envT, Hb + (size_t)c * tsz, t0, t1, gsm, gism);
           }
           const R* E = triv;
           int e = 3;   // index in Q of the buffer E lives in (none yet)
@@ -634,15 +683,15 @@ __global__ void __launch_bounds__(kThreads) k_mc(KArgs<R> a, uint64_t* S, int ns
             if (s1 != s2) {
               R w, wp;
               if (pass == 0) {
-                run_op<R>(OP_COL1_LEFT, D, Dc, E, Muc, tptr(a, i1, s1), Mdc, nullptr, X1, t0, t1);
-                run_op<R>(OP_COL1_LEFT, D, Dc, E, Muc, tptr(a, i1, s2), Mdc, nullptr, Xf, t0, t1);
+                run_op<R>(OP_COL1_LEFT, D, Dc, E, Muc, tptr(a, i1, s1), Mdc, nullptr, X1, t0, t1, gsm, gism);
+                run_op<R>(OP_COL1_LEFT, D, Dc, E, Muc, tptr(a, i1, s2), Mdc, nullptr, Xf, t0, t1, gsm, gism);
                 run_op<R>(OP_COL1_LEFT, D, Dc, Xf, Mu + (size_t)(c + 1) * envT, tptr(a, i2, s1),
-                          Md + (size_t)(c + 1) * envT, nullptr, X2, t0, t1);
+                          Md + (size_t)(c + 1) * envT, nullptr, X2, t0, t1, gsm, gism);
                 w = block_dot(X1, Hb + (size_t)(c + 1) * tsz, (int)tsz, red);
                 wp = block_dot(X2, Hb + (size_t)(c + 2) * tsz, (int)tsz, red);
               } else {
-                run_op<R>(OP_COL2_LEFT, D, Dc, E, Muc, tptr(a, i1, s1), tptr(a, i2, s2), Mdc, X1, t0, t1);
-                run_op<R>(OP_COL2_LEFT, D, Dc, E, Muc, tptr(a, i1, s2), tptr(a, i2, s1), Mdc, Xf, t0, t1);
+                run_op<R>(OP_COL2_LEFT, D, Dc, E, Muc, tptr(a, i1, s1), tptr(a, i2, s2), Mdc, X1, t0, t1, gsm, gism);
+                run_op<R>(OP_COL2_LEFT, D, Dc, E, Muc, tptr(a, i1, s2), tptr(a, i2, s1), Mdc, Xf, t0, t1, gsm, gism);
                 w = block_dot(X1, Hb + (size_t)(c + 1) * tsz, (int)tsz, red);
                 wp = block_dot(Xf, Hb + (size_t)(c + 1) * tsz, (int)tsz, red);
               }
@@ -668,9 +717,9 @@ __global__ void __launch_bounds__(kThreads) k_mc(KArgs<R> a, uint64_t* S, int ns
               __syncthreads();
             } else {
               if (pass == 0)
-                run_op<R>(OP_COL1_LEFT, D, Dc, E, Muc, tptr(a, i1, s1), Mdc, nullptr, X1, t0, t1);
+                run_op<R>(OP_COL1_LEFT, D, Dc, E, Muc, tptr(a, i1, s1), Mdc, nullptr, X1, t0, t1, gsm, gism);
               else
-                run_op<R>(OP_COL2_LEFT, D, Dc, E, Muc, tptr(a, i1, s1), tptr(a, i2, s2), Mdc, X1, t0, t1);
+                run_op<R>(OP_COL2_LEFT, D, Dc, E, Muc, tptr(a, i1, s1), tptr(a, i2, s2), Mdc, X1, t0, t1, gsm, gism);
               chosen = (e + 1) & 3;
             }
             e = chosen;
@@ -697,9 +746,8 @@ int max_blocks_boundary(const Geometry& g) {
   int dev = 0, nsm = 0, nb = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  size_t smem = wm_smem_bytes(g, sizeof(R));
-  if (smem > 160 * 1024) smem = 0;
-  if (smem) cudaFuncSetAttribute(k_boundary<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const size_t smem = dyn_smem_bytes(g, sizeof(R), wm_smem_bytes(g, sizeof(R)) <= 160 * 1024);
+  cudaFuncSetAttribute(k_boundary<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_boundary<R>, kThreads, smem);
   if (nb < 1) nb = 1;
   return nsm * nb;
@@ -707,11 +755,9 @@ int max_blocks_boundary(const Geometry& g) {
 
 template <typename R>
 cudaError_t launch_boundary(const KArgs<R>& a, int dirs, int grid, cudaStream_t st) {
-  const size_t smem = a.smem_wm ? wm_smem_bytes(a.g, sizeof(R)) : 0;
-  if (smem) {
-    cudaError_t e = cudaFuncSetAttribute(k_boundary<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-  }
+  const size_t smem = dyn_smem_bytes(a.g, sizeof(R), a.smem_wm != 0);
+  cudaError_t e = cudaFuncSetAttribute(k_boundary<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
   k_boundary<R><<<grid, kThreads, smem, st>>>(a, dirs);
   return cudaGetLastError();
 }
@@ -721,9 +767,8 @@ int max_blocks_mc(const Geometry& g) {
   int dev = 0, nsm = 0, nb = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  size_t smem = wm_smem_bytes(g, sizeof(R));
-  if (smem > 160 * 1024) smem = 0;
-  if (smem) cudaFuncSetAttribute(k_mc<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const size_t smem = dyn_smem_bytes(g, sizeof(R), wm_smem_bytes(g, sizeof(R)) <= 160 * 1024);
+  cudaFuncSetAttribute(k_mc<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_mc<R>, kThreads, smem);
   if (nb < 1) nb = 1;
   return nsm * nb;
@@ -732,24 +777,28 @@ int max_blocks_mc(const Geometry& g) {
 template <typename R>
 cudaError_t launch_mc(const KArgs<R>& a, uint64_t* S, int nsweeps, uint64_t seed, uint64_t chain0, uint64_t sweep0,
                       long long* accepted, int grid, cudaStream_t st) {
-  const size_t smem = a.smem_wm ? wm_smem_bytes(a.g, sizeof(R)) : 0;
-  if (smem) {
-    cudaError_t e = cudaFuncSetAttribute(k_mc<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-  }
+  const size_t smem = dyn_smem_bytes(a.g, sizeof(R), a.smem_wm != 0);
+  cudaError_t e = cudaFuncSetAttribute(k_mc<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
   k_mc<R><<<grid, kThreads, smem, st>>>(a, S, nsweeps, seed, chain0, sweep0, accepted);
   return cudaGetLastError();
 }
 
 template <typename R>
 cudaError_t launch_row(const KArgs<R>& a, int grid, cudaStream_t st) {
-  k_row<R><<<grid, kThreads, 0, st>>>(a);
+  const size_t smem = dyn_smem_bytes(a.g, sizeof(R), false);
+  cudaError_t e = cudaFuncSetAttribute(k_row<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_row<R><<<grid, kThreads, smem, st>>>(a);
   return cudaGetLastError();
 }
 
 template <typename R>
 cudaError_t launch_pair(const KArgs<R>& a, int grid, cudaStream_t st) {
-  k_pair<R><<<grid, kThreads, 0, st>>>(a);
+  const size_t smem = dyn_smem_bytes(a.g, sizeof(R), false);
+  cudaError_t e = cudaFuncSetAttribute(k_pair<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_pair<R><<<grid, kThreads, smem, st>>>(a);
   return cudaGetLastError();
 }
 

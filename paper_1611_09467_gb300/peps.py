@@ -58,6 +58,8 @@ def lib():
         "peps_gradient": [P, P, i, ctypes.POINTER(d), P, P, P, P, P, P, ctypes.POINTER(i)],
         "peps_mc_sweep": [P, P, i, i, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64, P],
         "peps_synchronize": [P],
+        "peps_profile_enable": [P, i],
+        "peps_profile_read": [P, P, P, i],
         "peps_debug_host_op": [i, i, i, P, P, P, P, P, P],
         "peps_debug_host_zip": [i, i, i, P, P, P, P, P],
     }
@@ -78,7 +80,8 @@ def exported_symbols():
     L = lib()
     names = ["peps_create", "peps_destroy", "peps_set_tensors", "peps_amplitudes", "peps_local_energy",
              "peps_log_derivatives", "peps_evaluate", "peps_gradient", "peps_mc_sweep", "peps_synchronize",
-             "peps_status_str", "peps_last_error", "peps_debug_host_op", "peps_debug_host_zip"]
+             "peps_status_str", "peps_last_error", "peps_debug_host_op", "peps_debug_host_zip",
+             "peps_profile_enable", "peps_profile_read"]
     return {n: hasattr(L, n) for n in names}
 
 
@@ -217,6 +220,19 @@ class PEPS:
         acc = torch.zeros(n, dtype=torch.int64, device=S.device)
         check(lib().peps_mc_sweep(self.h, _ptr(S), n, int(nsweeps), int(seed), int(chain0), int(sweep0), _ptr(acc)))
         return acc
+
+    KERNELS = ["boundary", "row_sandwich", "pair_sandwich", "finalize", "grad_accum", "energy_sum",
+               "grad_finalize", "mc_sweep"]
+
+    def profile(self, on=True):
+        check(lib().peps_profile_enable(self.h, 1 if on else 0))
+
+    def profile_read(self, reset=True):
+        """{kernel: (milliseconds, launches)} since the last reset (synchronises the stream)."""
+        ms = np.zeros(8, dtype=np.float64)
+        n = np.zeros(8, dtype=np.int64)
+        check(lib().peps_profile_read(self.h, _ptr(ms), _ptr(n), 1 if reset else 0))
+        return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(self.KERNELS)}
 
     def synchronize(self):
         check(lib().peps_synchronize(self.h))
