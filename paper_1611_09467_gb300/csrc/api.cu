@@ -103,6 +103,7 @@ struct peps_ctx {
   DevBuf A, triv_mps, triv_t1, triv_t2, bd;
   DevBuf env, small, O, scratch, gsum;
   int chunk = 0;  // configurations per pass
+  int res_boundary = 0, res_row = 0, res_pair = 0, res_mc = 0;  // resident CTAs per kernel
   // profiling: event pairs per kernel id
   bool prof = false;
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev;
@@ -260,18 +261,19 @@ peps_status evaluate_chunk(peps_ctx* c, const uint64_t* S, int n, bool need_env_
   a.O = O;
   PEPS_CUDA(cudaMemsetAsync(sm.flags, 0, (size_t)n * sizeof(int), c->stream));
   const int dirs = need_env_l ? 2 : 1;
-  int grid = std::min(n * dirs, std::min(c->nslots, max_blocks_boundary<R>(c->g)));
+  // persistent kernels: never more CTAs than can be resident at once
+  int grid = std::min(n * dirs, std::min(c->nslots, c->res_boundary));
   {
     Prof pf(c, 0);
     PEPS_CUDA(launch_boundary<R>(a, dirs, std::max(grid, 1), c->stream));
   }
   if (need_env_l) {
-    grid = std::min(n * c->g.Ly, c->nslots);
+    grid = std::min(n * c->g.Ly, std::min(c->nslots, c->res_row));
     Prof pf(c, 1);
     PEPS_CUDA(launch_row<R>(a, std::max(grid, 1), c->stream));
   }
   if (need_pairs && c->g.Ly > 1) {
-    grid = std::min(n * (c->g.Ly - 1), c->nslots);
+    grid = std::min(n * (c->g.Ly - 1), std::min(c->nslots, c->res_pair));
     Prof pf(c, 2);
     PEPS_CUDA(launch_pair<R>(a, std::max(grid, 1), c->stream));
   } else {
@@ -382,7 +384,7 @@ peps_status mc_impl(peps_ctx* c, uint64_t* S, int n, int nsweeps, uint64_t seed,
   Small sm;
   sm.carve(c->small.p, c->chunk, c->g.Ly);
   KArgs<R> a = make_args<R>(c, S, n, sm);
-  const int grid = std::min(n, std::min(c->nslots, max_blocks_mc<R>(c->g)));
+  const int grid = std::min(n, std::min(c->nslots, c->res_mc));
   Prof pf(c, 7);
   PEPS_CUDA(launch_mc<R>(a, S, nsweeps, seed, chain0, sweep0, (long long*)accepted, std::max(grid, 1), c->stream));
   return PEPS_OK;
@@ -451,8 +453,21 @@ peps_status peps_create(const peps_params* p, const double* A_host, void* stream
     delete c;
     return cuda_fail(e, "device query");
   }
-  c->wm_smem = wm_smem_bytes(c->g, c->elem) <= 160 * 1024;
-  c->nslots = c->nsm * 4;
+  c->wm_smem = wm_fits_smem(c->g, c->elem);
+  if (c->elem == 8) {
+    c->res_boundary = max_blocks_boundary<double>(c->g);
+    c->res_row = max_blocks_row<double>(c->g);
+    c->res_pair = max_blocks_pair_fused<double>(c->g);
+    if (!c->res_pair) c->res_pair = max_blocks_pair<double>(c->g);
+    c->res_mc = max_blocks_mc<double>(c->g);
+  } else {
+    c->res_boundary = max_blocks_boundary<float>(c->g);
+    c->res_row = max_blocks_row<float>(c->g);
+    c->res_pair = max_blocks_pair_fused<float>(c->g);
+    if (!c->res_pair) c->res_pair = max_blocks_pair<float>(c->g);
+    c->res_mc = max_blocks_mc<float>(c->g);
+  }
+  c->nslots = std::max(std::max(c->res_boundary, c->res_row), std::max(c->res_pair, c->res_mc));
   peps_status st = c->elem == 8 ? upload_tensors<double>(c, A_host) : upload_tensors<float>(c, A_host);
   if (st == PEPS_OK) st = c->elem == 8 ? setup_trivial<double>(c) : setup_trivial<float>(c);
   if (st != PEPS_OK) {

@@ -8,6 +8,11 @@
 
 #include "contract.cuh"
 
+// Phase markers inside the truncation; empty unless a timing harness defines them.
+#ifndef PEPS_PHASE
+#define PEPS_PHASE(k)
+#endif
+
 namespace peps {
 
 constexpr int kThreads = 256;
@@ -245,8 +250,10 @@ struct TruncWork {
   R* lam;     // Kmax
   R* Z;       // Kmax x 2Qmax
   R* lu;      // Kmax x 6 x 2Qmax
-  R* Ub;      // Qmax x Kmax
-  R* Uk;      // Pmax x Kmax
+  R* Ub;      // Qmax x Kmax (unused when Ubs is set)
+  R* Uk;      // Pmax x Kmax compact copy of the result in global memory
+  R* Ubs;     // Qmax x Kmax in shared memory (after the truncation matrix)
+  R* Uks;     // Pmax x Kmax in shared memory
   R* red;     // >= 64 (shared)
   R* wv;      // >= 256 (shared): reflector products
   R* gsm;     // GEMM shared scratch (may alias Wm: used only after the reflectors are dead)
@@ -302,79 +309,88 @@ __device__ int sturm_count(const R* t2, int n2, R x, R pivmin) {
 
 // Inverse iteration for one eigenvalue of the n2 x n2 zero-diagonal
 // symmetric tridiagonal with off-diagonal t: Gaussian elimination with
-// partial pivoting on (T - lam I), three solves from a fixed pseudo-random
-// start vector.  Sequential, one thread.
+// partial pivoting on (T - lam I), two solves from a fixed pseudo-random
+// start vector.  Sequential, one thread per eigenvalue; the workspace is
+// interleaved across the K threads (element i of thread k at i * K + k) so
+// the lock-step accesses of a warp are contiguous.
 template <typename R>
-__device__ void inverse_iteration(const R* t, int n2, R lam, R pivtiny, R* ws, R* z, unsigned seed) {
-  R* dd = ws;
-  R* du = ws + n2;
-  R* du2 = ws + 2 * n2;
-  R* mult = ws + 3 * n2;
-  R* piv = ws + 4 * n2;
-  R* b = ws + 5 * n2;
+__device__ void inverse_iteration(const R* t, int n2, R lam, R pivtiny, R* ws, int K, int k, R* z, int zs,
+                                  unsigned seed) {
+  const size_t st = (size_t)n2 * K;
+  R* dd = ws + k;
+  R* du = dd + st;
+  R* du2 = du + st;
+  R* mult = du2 + st;
+  R* piv = mult + st;
+  R* b = piv + st;
+#define IX(i) ((size_t)(i) * K)
   for (int i = 0; i < n2; ++i) {
-    dd[i] = -lam;
-    du[i] = i < n2 - 1 ? t[i] : R(0);
-    du2[i] = R(0);
+    dd[IX(i)] = -lam;
+    du[IX(i)] = i < n2 - 1 ? t[i] : R(0);
+    du2[IX(i)] = R(0);
   }
   for (int i = 0; i < n2 - 1; ++i) {
     const R sub = t[i];
-    R a = dd[i];
+    R a = dd[IX(i)];
     if (fabs(a) >= fabs(sub)) {
-      if (a == R(0)) a = dd[i] = pivtiny;
+      if (a == R(0)) a = dd[IX(i)] = pivtiny;
       const R l = sub / a;
-      mult[i] = l;
-      piv[i] = R(0);
-      dd[i + 1] -= l * du[i];
+      mult[IX(i)] = l;
+      piv[IX(i)] = R(0);
+      dd[IX(i + 1)] -= l * du[IX(i)];
     } else {
       const R l = a / sub;
-      mult[i] = l;
-      piv[i] = R(1);
-      dd[i] = sub;
-      const R tmp = du[i];
-      du[i] = dd[i + 1];
-      dd[i + 1] = tmp - l * dd[i + 1];
+      mult[IX(i)] = l;
+      piv[IX(i)] = R(1);
+      dd[IX(i)] = sub;
+      const R tmp = du[IX(i)];
+      du[IX(i)] = dd[IX(i + 1)];
+      dd[IX(i + 1)] = tmp - l * dd[IX(i + 1)];
       if (i < n2 - 2) {
-        du2[i] = du[i + 1];
-        du[i + 1] = -l * du[i + 1];
+        du2[IX(i)] = du[IX(i + 1)];
+        du[IX(i + 1)] = -l * du[IX(i + 1)];
       }
     }
   }
   for (int i = 0; i < n2; ++i) {
-    if (fabs(dd[i]) < pivtiny) dd[i] = dd[i] < R(0) ? -pivtiny : pivtiny;
-    dd[i] = R(1) / dd[i];   // stored as reciprocals for the solves
+    R v = dd[IX(i)];
+    if (fabs(v) < pivtiny) v = v < R(0) ? -pivtiny : pivtiny;
+    dd[IX(i)] = R(1) / v;   // stored as reciprocals for the solves
   }
-  // start vector
   unsigned h = seed * 2654435761u + 12345u;
   for (int i = 0; i < n2; ++i) {
     h ^= h << 13; h ^= h >> 17; h ^= h << 5;
-    b[i] = R((int)(h & 0xffffu) - 32768) / R(32768) + R(0.001);
+    b[IX(i)] = R((int)(h & 0xffffu) - 32768) / R(32768) + R(0.001);
   }
-  for (int it = 0; it < 3; ++it) {
+  for (int it = 0; it < 2; ++it) {
     for (int i = 0; i < n2 - 1; ++i) {
-      if (piv[i] == R(0)) {
-        b[i + 1] -= mult[i] * b[i];
+      if (piv[IX(i)] == R(0)) {
+        b[IX(i + 1)] -= mult[IX(i)] * b[IX(i)];
       } else {
-        const R tmp = b[i];
-        b[i] = b[i + 1];
-        b[i + 1] = tmp - mult[i] * b[i];
+        const R tmp = b[IX(i)];
+        b[IX(i)] = b[IX(i + 1)];
+        b[IX(i + 1)] = tmp - mult[IX(i)] * b[IX(i)];
       }
     }
-    b[n2 - 1] *= dd[n2 - 1];
-    if (n2 >= 2) b[n2 - 2] = (b[n2 - 2] - du[n2 - 2] * b[n2 - 1]) * dd[n2 - 2];
-    for (int i = n2 - 3; i >= 0; --i) b[i] = (b[i] - du[i] * b[i + 1] - du2[i] * b[i + 2]) * dd[i];
+    b[IX(n2 - 1)] *= dd[IX(n2 - 1)];
+    if (n2 >= 2) b[IX(n2 - 2)] = (b[IX(n2 - 2)] - du[IX(n2 - 2)] * b[IX(n2 - 1)]) * dd[IX(n2 - 2)];
+    for (int i = n2 - 3; i >= 0; --i)
+      b[IX(i)] = (b[IX(i)] - du[IX(i)] * b[IX(i + 1)] - du2[IX(i)] * b[IX(i + 2)]) * dd[IX(i)];
     R mx = R(0);
-    for (int i = 0; i < n2; ++i) mx = fmax(mx, fabs(b[i]));
+    for (int i = 0; i < n2; ++i) mx = fmax(mx, fabs(b[IX(i)]));
     if (!(mx > R(0))) mx = R(1);
+    const R imx = R(1) / mx;
     R ss = R(0);
     for (int i = 0; i < n2; ++i) {
-      b[i] /= mx;
-      ss += b[i] * b[i];
+      const R v = b[IX(i)] * imx;
+      b[IX(i)] = v;
+      ss += v * v;
     }
     const R inv = R(1) / dsqrt(ss);
-    for (int i = 0; i < n2; ++i) b[i] *= inv;
+    for (int i = 0; i < n2; ++i) b[IX(i)] *= inv;
   }
-  for (int i = 0; i < n2; ++i) z[i] = b[i];
+  for (int i = 0; i < n2; ++i) z[(size_t)i * zs] = b[IX(i)];
+#undef IX
 }
 
 // Writes U_K (m x K) through (uo_r, uo_c) and C' = U_K^T X (K x n) through
@@ -396,6 +412,7 @@ __device__ void cta_topk_left(const R* X, int m, int n, int K, TruncWork<R>& w, 
     __syncthreads();
     return;
   }
+  PEPS_PHASE(0);
   const bool tall = m >= n;
   const int P = tall ? m : n, Q = tall ? n : m;
   const int ld = w.ldw;
@@ -448,17 +465,23 @@ __device__ void cta_topk_left(const R* X, int m, int n, int K, TruncWork<R>& w, 
           const int cl = cb + tid / tpc, gl = tid % tpc;
           const bool act = cl < ncol;
           const int c = j + 1 + (act ? cl : 0);
-          R sacc = (gl == 0) ? W[j * ld + c] : R(0);
-          for (int i = j + 1 + gl; i < P; i += tpc) sacc += W[i * ld + j] * W[i * ld + c];
-          sacc = warp_sum(sacc, tpc);
+          R s0 = (gl == 0) ? W[j * ld + c] : R(0), s1 = R(0), s2 = R(0), s3 = R(0);
+          int i = j + 1 + gl;
+          for (; i + 3 * tpc < P; i += 4 * tpc) {
+            s0 += W[i * ld + j] * W[i * ld + c];
+            s1 += W[(i + tpc) * ld + j] * W[(i + tpc) * ld + c];
+            s2 += W[(i + 2 * tpc) * ld + j] * W[(i + 2 * tpc) * ld + c];
+            s3 += W[(i + 3 * tpc) * ld + j] * W[(i + 3 * tpc) * ld + c];
+          }
+          for (; i < P; i += tpc) s0 += W[i * ld + j] * W[i * ld + c];
+          R sacc = warp_sum((s0 + s1) + (s2 + s3), tpc);
           if (act && gl == 0) wv[c] = sacc * tau;
         }
         __syncthreads();
-        const int rows = P - j;
-        for (int e = tid; e < rows * ncol; e += blockDim.x) {
-          const int ii = e / ncol, c = j + 1 + e % ncol, i = j + ii;
-          const R v = ii == 0 ? R(1) : W[i * ld + j];
-          W[i * ld + c] -= wv[c] * v;
+        // rank-1 update: warps over rows, lanes over columns
+        for (int i = j + warp; i < P; i += kWarps) {
+          const R v = i == j ? R(1) : W[i * ld + j];
+          for (int c = j + 1 + lane; c < Q; c += 32) W[i * ld + c] -= wv[c] * v;
         }
       }
       __syncthreads();
@@ -496,21 +519,39 @@ __device__ void cta_topk_left(const R* X, int m, int n, int K, TruncWork<R>& w, 
           const int rl = rb + tid / tpc, gl = tid % tpc;
           const bool act = rl < nrow;
           const int i = j + 1 + (act ? rl : 0);
-          R sacc = (gl == 0) ? W[i * ld + j + 1] : R(0);
-          for (int c = j + 2 + gl; c < Q; c += tpc) sacc += W[i * ld + c] * W[j * ld + c];
-          sacc = warp_sum(sacc, tpc);
+          R s0 = (gl == 0) ? W[i * ld + j + 1] : R(0), s1 = R(0), s2 = R(0), s3 = R(0);
+          int c = j + 2 + gl;
+          for (; c + 3 * tpc < Q; c += 4 * tpc) {
+            s0 += W[i * ld + c] * W[j * ld + c];
+            s1 += W[i * ld + c + tpc] * W[j * ld + c + tpc];
+            s2 += W[i * ld + c + 2 * tpc] * W[j * ld + c + 2 * tpc];
+            s3 += W[i * ld + c + 3 * tpc] * W[j * ld + c + 3 * tpc];
+          }
+          for (; c < Q; c += tpc) s0 += W[i * ld + c] * W[j * ld + c];
+          R sacc = warp_sum((s0 + s1) + (s2 + s3), tpc);
           if (act && gl == 0) wv[i] = sacc * tau;
         }
         __syncthreads();
-        for (int e = tid; e < nrow * ncol; e += blockDim.x) {
-          const int i = j + 1 + e / ncol, cc = e % ncol, c = j + 1 + cc;
-          const R v = cc == 0 ? R(1) : W[j * ld + c];
-          W[i * ld + c] -= wv[i] * v;
+        // rank-1 update: warps over rows, lanes over columns (v' held per lane)
+        R vl[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+          const int c = j + 1 + lane + 32 * t;
+          vl[t] = c == j + 1 ? R(1) : (c < Q ? W[j * ld + c] : R(0));
+        }
+        for (int i = j + 1 + warp; i < P; i += kWarps) {
+          const R wi = wv[i];
+#pragma unroll
+          for (int t = 0; t < 8; ++t) {
+            const int c = j + 1 + lane + 32 * t;
+            if (c < Q) W[i * ld + c] -= wi * vl[t];
+          }
         }
       }
       __syncthreads();
     }
   }
+  PEPS_PHASE(1);
   // ---------------- Sturm bisection for the K largest singular values
   const int n2 = 2 * Q;
   R tmax = R(0);
@@ -553,17 +594,17 @@ __device__ void cta_topk_left(const R* X, int m, int n, int K, TruncWork<R>& w, 
     if (gid < K && gl == 0) w.lam[gid] = R(0.5) * (lo + hi);
   }
   __syncthreads();
+  PEPS_PHASE(2);
   // ---------------- inverse iteration, one thread per vector
   const R pivtiny = Eps<R>::eps * fmax(tmax, Eps<R>::tiny * R(1e10));
-  if (tid < K)
-    inverse_iteration(w.t, n2, w.lam[tid], pivtiny, w.lu + (size_t)tid * 6 * n2, w.Z + (size_t)tid * n2,
-                      (unsigned)(tid + 1));
+  if (tid < K) inverse_iteration(w.t, n2, w.lam[tid], pivtiny, w.lu, K, tid, w.Z + tid, K, (unsigned)(tid + 1));
   __syncthreads();
+  PEPS_PHASE(3);
   // extract u-parts (odd positions) for a tall matrix, v-parts (even) for a wide one
-  R* Ub = w.Ub;
+  R* Ub = w.Ubs;
   for (int e = tid; e < Q * K; e += blockDim.x) {
     const int i = e / K, k = e % K;
-    Ub[e] = w.Z[(size_t)k * n2 + 2 * i + (tall ? 1 : 0)];
+    Ub[e] = w.Z[(size_t)(2 * i + (tall ? 1 : 0)) * K + k];
   }
   __syncthreads();
   // ---------------- Gram-Schmidt with re-orthogonalisation (CGS2)
@@ -605,8 +646,9 @@ __device__ void cta_topk_left(const R* X, int m, int n, int K, TruncWork<R>& w, 
       __syncthreads();
     }
   }
+  PEPS_PHASE(4);
   // ---------------- back-transformation, one thread group per column
-  R* Uk = w.Uk;
+  R* Uk = w.Uks;
   const int rowsU = tall ? P : Q;
   for (int e = tid; e < rowsU * K; e += blockDim.x) {
     const int i = e / K, k = e % K;
@@ -649,14 +691,19 @@ __device__ void cta_topk_left(const R* X, int m, int n, int K, TruncWork<R>& w, 
     }
   }
   __syncthreads();
+  PEPS_PHASE(5);
   // ---------------- outputs
   for (int e = tid; e < m * K; e += blockDim.x) {
     const int i = e / K, k = e % K;
-    Uout[ixoff(uo_r, i) + ixoff(uo_c, k)] = Uk[e];
+    const R v = Uk[e];
+    Uout[ixoff(uo_r, i) + ixoff(uo_c, k)] = v;
+    w.Uk[e] = v;
   }
+  __syncthreads();
   // C' = U_K^T X
   GemmDesc g = gemm(K, n, m, ix1(1), kx(m, 0, K), kx(m, 0, n), ix1(1), co_r, co_c);
-  cta_gemm<R>(g, Uk, X, Cout, false, w.gsm, w.gism);
+  cta_gemm<R>(g, w.Uk, X, Cout, false, w.gsm, w.gism);
+  PEPS_PHASE(6);
 }
 
 }  // namespace peps

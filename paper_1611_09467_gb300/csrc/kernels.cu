@@ -22,6 +22,7 @@
 
 #include "device.cuh"
 #include "kernels.h"
+#include "pair_fused.cuh"
 
 namespace peps {
 
@@ -51,27 +52,37 @@ size_t wm_smem_bytes(const Geometry& g, size_t elem) {
   return P * (P + 1) * elem;
 }
 
-// Dynamic shared memory of a kernel: a region of reals (the truncation
-// matrix when it lives in shared memory, or the GEMM tiles; the two are never
-// live together) followed by the GEMM offset tables.
-size_t dyn_smem_bytes(const Geometry& g, size_t elem, bool with_wm) {
-  size_t reals = (size_t)kGemmSmemReals * elem;
-  if (with_wm) reals = std::max(reals, wm_smem_bytes(g, elem));
-  reals = (reals + 15) / 16 * 16;
-  return reals + (size_t)kGemmSmemInts * sizeof(int);
+// Dynamic shared memory of a kernel: a region of reals followed by the GEMM
+// offset tables.  For the kernels that truncate, the reals hold (truncation
+// matrix if it fits) + the two singular-vector blocks during a truncation and
+// the GEMM tiles otherwise; the two uses are never live together.
+__host__ __device__ inline size_t trunc_smem_reals(const Geometry& g, bool wm_in_smem) {
+  const size_t P = (size_t)g.Dc * g.D;
+  return (wm_in_smem ? P * (P + 1) : 0) + 2 * P * (size_t)g.Dc;
+}
+
+__host__ __device__ inline size_t reals_region_bytes(const Geometry& g, size_t elem, bool truncates, bool wm_in_smem) {
+  size_t r = (size_t)kGemmSmemReals;
+  if (truncates) {
+    const size_t t = trunc_smem_reals(g, wm_in_smem);
+    r = r > t ? r : t;
+  }
+  return (r * elem + 15) / 16 * 16;
+}
+
+size_t dyn_smem_bytes(const Geometry& g, size_t elem, bool truncates, bool wm_in_smem) {
+  return reals_region_bytes(g, elem, truncates, wm_in_smem) + (size_t)kGemmSmemInts * sizeof(int);
+}
+
+bool wm_fits_smem(const Geometry& g, size_t elem) {
+  return dyn_smem_bytes(g, elem, true, true) <= 200 * 1024;
 }
 
 template <typename R>
-__device__ __forceinline__ void smem_split(unsigned char* raw, const Geometry& g, bool with_wm, R*& reals, int*& ints) {
-  size_t rb = (size_t)kGemmSmemReals * sizeof(R);
-  if (with_wm) {
-    const size_t P = (size_t)g.Dc * g.D;
-    const size_t wb = P * (P + 1) * sizeof(R);
-    rb = rb > wb ? rb : wb;
-  }
-  rb = (rb + 15) / 16 * 16;
+__device__ __forceinline__ void smem_split(unsigned char* raw, const Geometry& g, bool truncates, bool wm_in_smem,
+                                           R*& reals, int*& ints) {
   reals = reinterpret_cast<R*>(raw);
-  ints = reinterpret_cast<int*>(raw + rb);
+  ints = reinterpret_cast<int*>(raw + reals_region_bytes(g, sizeof(R), truncates, wm_in_smem));
 }
 
 static size_t zip_elems(const Geometry& g, bool wm_in_smem) {
@@ -224,11 +235,15 @@ __device__ void carve_zip(const Geometry& g, R*& p, ZipBufs<R>& zb, R* wm_smem, 
   zb.X = p; p += P * P;
   TruncWork<R>& w = zb.tw;
   w.ldw = (int)P + 1;
+  R* sh = gsm;   // shared reals region: [Wm][Ubs][Uks]
   if (wm_smem) {
-    w.Wm = wm_smem;
+    w.Wm = sh;
+    sh += P * (P + 1);
   } else {
     w.Wm = p; p += P * (P + 1);
   }
+  w.Ubs = sh; sh += P * Dc;
+  w.Uks = sh;
   w.Qmax = (int)P;
   w.tau = p; p += 2 * P;
   w.t = p; p += 2 * P;
@@ -258,7 +273,7 @@ __global__ void __launch_bounds__(kThreads) k_boundary(KArgs<R> a, int dirs) {
   __shared__ R wv[kMaxDcD];
   R* gsm;
   int* gism;
-  smem_split<R>(smem_raw, g, a.smem_wm != 0, gsm, gism);
+  smem_split<R>(smem_raw, g, true, a.smem_wm != 0, gsm, gism);
   carve_zip<R>(g, p, zb, a.smem_wm ? gsm : nullptr, red, dred, wv, gsm, gism);
   R* lastbuf = p;
   for (int i = threadIdx.x; i <= Lx; i += blockDim.x) ones[i] = 1;
@@ -334,7 +349,7 @@ __global__ void __launch_bounds__(kThreads) k_row(KArgs<R> a) {
   const int envT = Dc * D * Dc, D4 = D * D * D * D;
   R* gsm;
   int* gism;
-  smem_split<R>(smem_raw, g, false, gsm, gism);
+  smem_split<R>(smem_raw, g, false, false, gsm, gism);
   R* p = a.scratch + (size_t)blockIdx.x * a.slot_elems;
   R* Gb = p; p += (size_t)(Lx + 1) * envT;
   R* F0 = p; p += envT;
@@ -407,7 +422,7 @@ __global__ void __launch_bounds__(kThreads) k_pair(KArgs<R> a) {
   const int envT = Dc * D * Dc, envT2 = Dc * D * D * Dc;
   R* gsm;
   int* gism;
-  smem_split<R>(smem_raw, g, false, gsm, gism);
+  smem_split<R>(smem_raw, g, false, false, gsm, gism);
   R* p = a.scratch + (size_t)blockIdx.x * a.slot_elems;
   R* Hb = p; p += (size_t)(Lx + 1) * envT2;
   R* E0 = p; p += envT2;
@@ -466,6 +481,84 @@ __global__ void __launch_bounds__(kThreads) k_pair(KArgs<R> a) {
       }
       if (c < Lx - 1) {
         run_op<R>(OP_COL2_LEFT, D, Dc, E, Muc, tptr(a, i1, a1), tptr(a, i2, a2), Mdc, En, t0, t1, gsm, gism);
+        E = En;
+        En = (En == E0) ? E1 : E0;
+      }
+    }
+    if (threadIdx.x == 0) {
+      a.eloc_v[(size_t)cfg * Ly + r] = ev;
+      if (!ok) atomicOr(&a.flags[cfg], kFlagZeroW);
+    }
+  }
+}
+
+// ------------------------------------------------------------ k_pair_fused
+// k_pair with the fused shared-memory transfer step (pair_fused.cuh) for a
+// fixed (D, Dc).  Transfers are stored [x'][x][y1][y2] (see pair_fused.cuh).
+template <typename R, int D, int Dc>
+__global__ void __launch_bounds__(kThreads) k_pair_fused(KArgs<R> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ R red[64];
+  __shared__ uint64_t sp[kMaxWords];
+  R* sm = reinterpret_cast<R*>(smem_raw);
+  const Geometry& g = a.g;
+  const int Lx = g.Lx, Ly = g.Ly;
+  constexpr int envT = Dc * D * Dc, envT2 = Dc * D * D * Dc;
+  R* p = a.scratch + (size_t)blockIdx.x * a.slot_elems;
+  R* Hb = p; p += (size_t)(Lx + 1) * envT2;
+  R* E0 = p; p += envT2;
+  R* E1 = p; p += envT2;
+  R* X1 = p;
+  const int npairs = Ly - 1;
+  for (int item = blockIdx.x; item < a.n * npairs; item += gridDim.x) {
+    const int cfg = item / npairs, r = item % npairs;
+    __syncthreads();
+    for (int i = threadIdx.x; i < g.nwords; i += blockDim.x) sp[i] = a.S[(size_t)cfg * g.nwords + i];
+    for (int e = threadIdx.x; e < envT2; e += blockDim.x) Hb[(size_t)Lx * envT2 + e] = a.triv_t2[e];
+    __syncthreads();
+    const R* Mu = r == 0 ? a.triv_mps : a.envU + ((size_t)cfg * Ly + (r - 1)) * Lx * envT;
+    const R* Md = r + 2 > Ly - 1 ? a.triv_mps : a.envL + ((size_t)cfg * Ly + (r + 2)) * Lx * envT;
+    for (int c = Lx - 1; c >= 0; --c) {
+      const int s1 = r * Lx + c, s2 = (r + 1) * Lx + c;
+      pair_step_fused<R, D, Dc>(true, Hb + (size_t)(c + 1) * envT2, Hb + (size_t)c * envT2, Mu + (size_t)c * envT,
+                                tptr(a, s1, spin_of(sp, s1)), tptr(a, s2, spin_of(sp, s2)), Md + (size_t)c * envT,
+                                nullptr, sm, red);
+    }
+    const R W = Hb[0];
+    const bool ok = W != R(0);
+    double ev = 0.0;
+    const R* E = a.triv_t2;
+    R* En = E0;
+    for (int c = 0; c < Lx; ++c) {
+      const int i1 = r * Lx + c, i2 = (r + 1) * Lx + c;
+      const int a1 = spin_of(sp, i1), a2 = spin_of(sp, i2);
+      const R* Muc = Mu + (size_t)c * envT;
+      const R* Mdc = Md + (size_t)c * envT;
+      if (a1 != a2) {  // vertical pair (r,c)-(r+1,c)
+        const R wp = pair_step_fused<R, D, Dc>(false, E, nullptr, Muc, tptr(a, i1, a2), tptr(a, i2, a1), Mdc,
+                                               Hb + (size_t)(c + 1) * envT2, sm, red);
+        if (ok) ev += 0.5 * g.J1 * ((double)wp / (double)W);
+      }
+      if (c < Lx - 1 && g.J2 != 0.0) {
+        const int j1 = i1 + 1, j2 = i2 + 1;
+        const int b1 = spin_of(sp, j1), b2 = spin_of(sp, j2);
+        const R* Mun = Mu + (size_t)(c + 1) * envT;
+        const R* Mdn = Md + (size_t)(c + 1) * envT;
+        if (a1 != b2) {  // diagonal (r,c)-(r+1,c+1)
+          pair_step_fused<R, D, Dc>(false, E, X1, Muc, tptr(a, i1, b2), tptr(a, i2, a2), Mdc, nullptr, sm, red);
+          const R wp = pair_step_fused<R, D, Dc>(false, X1, nullptr, Mun, tptr(a, j1, b1), tptr(a, j2, a1), Mdn,
+                                                 Hb + (size_t)(c + 2) * envT2, sm, red);
+          if (ok) ev += 0.5 * g.J2 * ((double)wp / (double)W);
+        }
+        if (b1 != a2) {  // anti-diagonal (r,c+1)-(r+1,c)
+          pair_step_fused<R, D, Dc>(false, E, X1, Muc, tptr(a, i1, a1), tptr(a, i2, b1), Mdc, nullptr, sm, red);
+          const R wp = pair_step_fused<R, D, Dc>(false, X1, nullptr, Mun, tptr(a, j1, a2), tptr(a, j2, b2), Mdn,
+                                                 Hb + (size_t)(c + 2) * envT2, sm, red);
+          if (ok) ev += 0.5 * g.J2 * ((double)wp / (double)W);
+        }
+      }
+      if (c < Lx - 1) {
+        pair_step_fused<R, D, Dc>(false, E, En, Muc, tptr(a, i1, a1), tptr(a, i2, a2), Mdc, nullptr, sm, red);
         E = En;
         En = (En == E0) ? E1 : E0;
       }
@@ -620,7 +713,7 @@ __global__ void __launch_bounds__(kThreads) k_mc(KArgs<R> a, uint64_t* S, int ns
   __shared__ R wv[kMaxDcD];
   R* gsm;
   int* gism;
-  smem_split<R>(smem_raw, g, a.smem_wm != 0, gsm, gism);
+  smem_split<R>(smem_raw, g, true, a.smem_wm != 0, gsm, gism);
   carve_zip<R>(g, p, zb, a.smem_wm ? gsm : nullptr, red, dred, wv, gsm, gism);
   R* Hb = p; p += (size_t)(Lx + 1) * envT2;
   R* Q[4];
@@ -746,7 +839,7 @@ int max_blocks_boundary(const Geometry& g) {
   int dev = 0, nsm = 0, nb = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  const size_t smem = dyn_smem_bytes(g, sizeof(R), wm_smem_bytes(g, sizeof(R)) <= 160 * 1024);
+  const size_t smem = dyn_smem_bytes(g, sizeof(R), true, wm_fits_smem(g, sizeof(R)));
   cudaFuncSetAttribute(k_boundary<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_boundary<R>, kThreads, smem);
   if (nb < 1) nb = 1;
@@ -755,7 +848,7 @@ int max_blocks_boundary(const Geometry& g) {
 
 template <typename R>
 cudaError_t launch_boundary(const KArgs<R>& a, int dirs, int grid, cudaStream_t st) {
-  const size_t smem = dyn_smem_bytes(a.g, sizeof(R), a.smem_wm != 0);
+  const size_t smem = dyn_smem_bytes(a.g, sizeof(R), true, a.smem_wm != 0);
   cudaError_t e = cudaFuncSetAttribute(k_boundary<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   k_boundary<R><<<grid, kThreads, smem, st>>>(a, dirs);
@@ -767,7 +860,7 @@ int max_blocks_mc(const Geometry& g) {
   int dev = 0, nsm = 0, nb = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  const size_t smem = dyn_smem_bytes(g, sizeof(R), wm_smem_bytes(g, sizeof(R)) <= 160 * 1024);
+  const size_t smem = dyn_smem_bytes(g, sizeof(R), true, wm_fits_smem(g, sizeof(R)));
   cudaFuncSetAttribute(k_mc<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_mc<R>, kThreads, smem);
   if (nb < 1) nb = 1;
@@ -777,7 +870,7 @@ int max_blocks_mc(const Geometry& g) {
 template <typename R>
 cudaError_t launch_mc(const KArgs<R>& a, uint64_t* S, int nsweeps, uint64_t seed, uint64_t chain0, uint64_t sweep0,
                       long long* accepted, int grid, cudaStream_t st) {
-  const size_t smem = dyn_smem_bytes(a.g, sizeof(R), a.smem_wm != 0);
+  const size_t smem = dyn_smem_bytes(a.g, sizeof(R), true, a.smem_wm != 0);
   cudaError_t e = cudaFuncSetAttribute(k_mc<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   k_mc<R><<<grid, kThreads, smem, st>>>(a, S, nsweeps, seed, chain0, sweep0, accepted);
@@ -785,17 +878,86 @@ cudaError_t launch_mc(const KArgs<R>& a, uint64_t* S, int nsweeps, uint64_t seed
 }
 
 template <typename R>
+int max_blocks_row(const Geometry& g) {
+  int dev = 0, nsm = 0, nb = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const size_t smem = dyn_smem_bytes(g, sizeof(R), false, false);
+  cudaFuncSetAttribute(k_row<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_row<R>, kThreads, smem);
+  return nsm * (nb < 1 ? 1 : nb);
+}
+
+template <typename R>
+int max_blocks_pair(const Geometry& g) {
+  int dev = 0, nsm = 0, nb = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const size_t smem = dyn_smem_bytes(g, sizeof(R), false, false);
+  cudaFuncSetAttribute(k_pair<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pair<R>, kThreads, smem);
+  return nsm * (nb < 1 ? 1 : nb);
+}
+
+template <typename R>
 cudaError_t launch_row(const KArgs<R>& a, int grid, cudaStream_t st) {
-  const size_t smem = dyn_smem_bytes(a.g, sizeof(R), false);
+  const size_t smem = dyn_smem_bytes(a.g, sizeof(R), false, false);
   cudaError_t e = cudaFuncSetAttribute(k_row<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   k_row<R><<<grid, kThreads, smem, st>>>(a);
   return cudaGetLastError();
 }
 
+template <typename R, int D, int Dc>
+static cudaError_t launch_pair_fused(const KArgs<R>& a, int grid, cudaStream_t st) {
+  const size_t smem = (size_t)PairSmem<D, Dc>::total * sizeof(R);
+  cudaError_t e = cudaFuncSetAttribute(k_pair_fused<R, D, Dc>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_pair_fused<R, D, Dc><<<grid, kThreads, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename R, int D, int Dc>
+static int fused_blocks() {
+  int dev = 0, nsm = 0, nb = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const size_t smem = (size_t)PairSmem<D, Dc>::total * sizeof(R);
+  cudaFuncSetAttribute(k_pair_fused<R, D, Dc>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pair_fused<R, D, Dc>, kThreads, smem);
+  return nsm * (nb < 1 ? 1 : nb);
+}
+
+// (D, Dc) pairs with a fused two-row step; FP64 only where its shared memory fits.
+template <typename R>
+static int pair_fused_id(const Geometry& g) {
+  if (g.D == 2 && g.Dc == 4) return 1;
+  if (g.D == 4 && g.Dc == 8) return 2;
+  if (sizeof(R) == 4 && g.D == 6 && g.Dc == 12) return 3;
+  if (sizeof(R) == 4 && g.D == 8 && g.Dc == 16) return 4;
+  return 0;
+}
+
+template <typename R>
+int max_blocks_pair_fused(const Geometry& g) {
+  switch (pair_fused_id<R>(g)) {
+    case 1: return fused_blocks<R, 2, 4>();
+    case 2: return fused_blocks<R, 4, 8>();
+    case 3: return fused_blocks<R, sizeof(R) == 4 ? 6 : 2, sizeof(R) == 4 ? 12 : 4>();
+    case 4: return fused_blocks<R, sizeof(R) == 4 ? 8 : 2, sizeof(R) == 4 ? 16 : 4>();
+  }
+  return 0;
+}
+
 template <typename R>
 cudaError_t launch_pair(const KArgs<R>& a, int grid, cudaStream_t st) {
-  const size_t smem = dyn_smem_bytes(a.g, sizeof(R), false);
+  switch (pair_fused_id<R>(a.g)) {
+    case 1: return launch_pair_fused<R, 2, 4>(a, grid, st);
+    case 2: return launch_pair_fused<R, 4, 8>(a, grid, st);
+    case 3: return launch_pair_fused<R, sizeof(R) == 4 ? 6 : 2, sizeof(R) == 4 ? 12 : 4>(a, grid, st);
+    case 4: return launch_pair_fused<R, sizeof(R) == 4 ? 8 : 2, sizeof(R) == 4 ? 16 : 4>(a, grid, st);
+  }
+  const size_t smem = dyn_smem_bytes(a.g, sizeof(R), false, false);
   cudaError_t e = cudaFuncSetAttribute(k_pair<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   k_pair<R><<<grid, kThreads, smem, st>>>(a);
@@ -833,6 +995,9 @@ cudaError_t launch_grad_finalize(int total, int, const double* sums, const doubl
 #define PEPS_INST(R)                                                                                    \
   template int max_blocks_boundary<R>(const Geometry&);                                                 \
   template int max_blocks_mc<R>(const Geometry&);                                                       \
+  template int max_blocks_row<R>(const Geometry&);                                                      \
+  template int max_blocks_pair<R>(const Geometry&);                                                     \
+  template int max_blocks_pair_fused<R>(const Geometry&);                                               \
   template cudaError_t launch_mc<R>(const KArgs<R>&, uint64_t*, int, uint64_t, uint64_t, uint64_t,      \
                                     long long*, int, cudaStream_t);                                      \
   template cudaError_t launch_boundary<R>(const KArgs<R>&, int, int, cudaStream_t);                     \

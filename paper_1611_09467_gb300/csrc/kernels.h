@@ -58,6 +58,7 @@ size_t row_slot_elems(const Geometry& g);
 size_t pair_slot_elems(const Geometry& g);
 size_t mc_slot_elems(const Geometry& g, bool wm_in_smem);
 size_t wm_smem_bytes(const Geometry& g, size_t elem);
+bool wm_fits_smem(const Geometry& g, size_t elem);
 
 template <typename R> cudaError_t launch_boundary(const KArgs<R>& a, int dirs, int grid, cudaStream_t st);
 template <typename R> cudaError_t launch_row(const KArgs<R>& a, int grid, cudaStream_t st);
@@ -67,6 +68,9 @@ template <typename R> cudaError_t launch_mc(const KArgs<R>& a, uint64_t* S, int 
                                             int grid, cudaStream_t st);
 template <typename R> int max_blocks_boundary(const Geometry& g);
 template <typename R> int max_blocks_mc(const Geometry& g);
+template <typename R> int max_blocks_row(const Geometry& g);
+template <typename R> int max_blocks_pair(const Geometry& g);
+template <typename R> int max_blocks_pair_fused(const Geometry& g);   // 0: no fused step for (D, Dc)
 template <typename R> cudaError_t launch_grad_accum(const GradArgs& a, const R* O, cudaStream_t st);
 
 cudaError_t launch_finalize(const Geometry& g, const uint64_t* S, int n, const double* eloc_h,

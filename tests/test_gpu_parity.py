@@ -57,6 +57,7 @@ CASES_FP64 = [
     (4, 5, 2, 3, 0.5, 12, True, 78),           # rectangular, odd width, truncated
     (5, 4, 3, 9, 0.0, 8, False, 79),           # J2 = 0, exact
     (2, 6, 2, 2, 0.5, 10, False, 80),          # two rows only, truncated
+    (6, 5, 4, 8, 0.5, 6, True, 81),            # fused two-row step (D=4, Dc=8), truncated
 ]
 
 
