@@ -140,6 +140,31 @@ peps_status peps_mc_sweep(peps_ctx* ctx, uint64_t* S_dev, int n, int nsweeps, ui
 peps_status peps_profile_enable(peps_ctx* ctx, int on);
 peps_status peps_profile_read(peps_ctx* ctx, double* ms /* [8] */, long long* launches /* [8] */, int reset);
 
+/* Allocation-free amplitudes.  The paper has no counterpart to this call: it
+ * exists for callers that cannot call cudaMalloc, such as code running inside
+ * another runtime's memory arena (framework custom ops, plugins, engines) or
+ * real-time code that must not allocate after start-up.  It computes what
+ * peps_amplitudes computes (ln|psi| and sign from the top-down boundary-MPS
+ * sweep) without a context and without allocating: the per-CTA scratch is a
+ * file-scope static device array of 8 MiB that every GPU loading the
+ * library holds until exit (a 16x16 D=8 Dc=16 FP32 slot takes 0.54 MB, so
+ * 15 CTAs run at once; FP64 with Dc*D = 256 on 64 columns does not fit).
+ *   params     lattice, D, Dc, prec (PEPS_FP64 or PEPS_FP32); J1, J2 unused.
+ *   A_dev      device [N][2][D^4] site tensors in the precision of prec
+ *              (double or float), padded as for peps_create.
+ *   S_dev      device [n][ceil(N/64)] configurations.
+ *   logabs_dev, sign_dev: device [n] outputs; status_dev: device [n] or NULL.
+ *   cuda_stream: a cudaStream_t (NULL = legacy default stream).
+ * Lattices whose per-CTA scratch exceeds the static array are rejected with
+ * PEPS_EINVAL and a message naming the sizes.  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress) with that
+ * device current; make that first call before any stream capture.  Every
+ * call shares the one array and leaves its contents behind (the kernel
+ * writes everything before reading it), so calls that overlap on the GPU,
+ * on any stream, race: serialise them. */
+peps_status peps_amplitudes_static(const peps_params* params, const void* A_dev, const uint64_t* S_dev, int n,
+                                   double* logabs_dev, int8_t* sign_dev, int32_t* status_dev, void* cuda_stream);
+
 /* Waits for the context's stream. */
 peps_status peps_synchronize(peps_ctx* ctx);
 

@@ -26,6 +26,14 @@ peps_status cuda_fail(cudaError_t e, const char* where) {
   return e == cudaErrorMemoryAllocation ? PEPS_ENOMEM : PEPS_ECUDA;
 }
 
+}  // namespace
+
+namespace peps {
+void set_last_error(const char* msg) { g_err = msg ? msg : ""; }
+}  // namespace peps
+
+namespace {
+
 #define PEPS_CUDA(call)                                  \
   do {                                                   \
     cudaError_t e_ = (call);                             \

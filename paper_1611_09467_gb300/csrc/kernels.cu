@@ -19,6 +19,10 @@
 // scratch slots bound the workspace.
 #include <algorithm>
 #include <cstdio>
+#include <cstring>
+#include <mutex>
+
+#include "../../include/peps.h"
 
 #include "device.cuh"
 #include "kernels.h"
@@ -1008,3 +1012,240 @@ PEPS_INST(double)
 PEPS_INST(float)
 
 }  // namespace peps
+
+// ===================================================================
+// Allocation-free amplitudes.
+//
+// Some callers cannot call cudaMalloc: code that runs inside another
+// runtime's memory arena (a framework custom op, a plugin, a game or
+// simulation engine) where a stray allocation would fragment or bypass the
+// owner's allocator, or real-time code that must not allocate after start-up.
+// peps_amplitudes_static serves them: it computes ln|psi| and sign with the
+// top-down boundary-MPS sweep (the k_boundary sweep without the stored
+// environments) and takes its per-CTA scratch from the file-scope array
+// below instead of the context workspace.  The caller passes the site
+// tensors, the configurations and the outputs, all in device memory.
+// ===================================================================
+namespace peps {
+
+constexpr size_t kStaticScratchBytes = size_t(8) << 20;   // 8 MiB on every device that loads the library
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+// Bond dimensions of the boundary MPS after absorbing one row (top-down),
+// the same rule K = min(Dc, rows, cols) the truncation applies.
+__device__ void next_bonds(const int* bin, int* bout, int Lx, int D, int Dc, int outdim, bool lr) {
+  for (int c = 0; c <= Lx; ++c) bout[c] = 1;
+  int k = 1;
+  if (lr) {
+    for (int c = 0; c < Lx - 1; ++c) {
+      const int K = min(Dc, min(k * outdim, bin[c + 1] * D));
+      bout[c + 1] = K;
+      k = K;
+    }
+  } else {
+    for (int c = Lx - 1; c > 0; --c) {
+      const int K = min(Dc, min(outdim * k, bin[c] * D));
+      bout[c] = K;
+      k = K;
+    }
+  }
+}
+
+__host__ __device__ inline size_t static_slot_elems(const Geometry& g, bool wm_in_smem) {
+  const size_t envT = (size_t)g.Dc * g.D * g.Dc, Dc = g.Dc, D = g.D, P = Dc * D;
+  const size_t zip = 2 * Dc * Dc * D + Dc * Dc * D * D + P * P + trunc_ws_elems((int)P, g.Dc, !wm_in_smem);
+  return (zip + 2 * (size_t)g.Lx * envT + 63) / 64 * 64;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kThreads) k_amplitudes_static(KArgs<R> a, R* scratch, size_t slot_elems) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ R red[64];
+  __shared__ uint64_t sp[kMaxWords];
+  __shared__ int bonds[2][kMaxDcD + 1];
+  __shared__ double dred[kWarps];
+  __shared__ R wv[kMaxDcD];
+  __shared__ R vec[kMaxDc], nv[kMaxDc];
+  const Geometry& g = a.g;
+  const int Lx = g.Lx, Ly = g.Ly, Dc = g.Dc, D = g.D;
+  const size_t envT = (size_t)Dc * D * Dc;
+  R* gsm;
+  int* gism;
+  smem_split<R>(smem_raw, g, true, a.smem_wm != 0, gsm, gism);
+  R* p = scratch + (size_t)blockIdx.x * slot_elems;
+  ZipBufs<R> zb;
+  carve_zip<R>(g, p, zb, a.smem_wm ? gsm : nullptr, red, dred, wv, gsm, gism);
+  R* Mbuf[2];
+  Mbuf[0] = p;
+  Mbuf[1] = p + (size_t)Lx * envT;
+  for (int cfg = blockIdx.x; cfg < a.n; cfg += gridDim.x) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < g.nwords; i += blockDim.x) sp[i] = a.S[(size_t)cfg * g.nwords + i];
+    // every buffer is written before it is read: the trivial MPS is rebuilt here
+    for (size_t e = threadIdx.x; e < (size_t)Lx * envT; e += blockDim.x) Mbuf[0][e] = (e % envT) == 0 ? R(1) : R(0);
+    for (int c = threadIdx.x; c <= Lx; c += blockDim.x) bonds[0][c] = 1;
+    __syncthreads();
+    double ls = 0.0;
+    bool zero = false;
+    int cur = 0;
+    for (int r = 0; r < Ly; ++r) {
+      const bool lr = (r % 2) == 0;
+      const double nrm = absorb_row<R>(a, Mbuf[cur], Mbuf[cur ^ 1], r, 0, lr, bonds[cur], sp, zb, red);
+      if (!(nrm > 0.0)) zero = true;
+      else ls += log(nrm);
+      if (threadIdx.x == 0) next_bonds(bonds[cur], bonds[cur ^ 1], Lx, D, Dc, r == Ly - 1 ? 1 : D, lr);
+      __syncthreads();
+      cur ^= 1;
+    }
+    if (threadIdx.x == 0) {
+      const R* Ml = Mbuf[cur];
+      vec[0] = R(1);
+      int na = 1;
+      for (int c = 0; c < Lx; ++c) {
+        const int nb = bonds[cur][c + 1];
+        const R* M = Ml + (size_t)c * envT;
+        for (int b = 0; b < nb; ++b) {
+          R s = R(0);
+          for (int x = 0; x < na; ++x) s += vec[x] * M[(size_t)x * D * Dc + b];
+          nv[b] = s;
+        }
+        for (int b = 0; b < nb; ++b) vec[b] = nv[b];
+        na = nb;
+      }
+      int pc = 0;
+      for (int w = 0; w < g.nwords; ++w) {
+        uint64_t word = sp[w];
+        if (w == g.nwords - 1 && (g.N & 63)) word &= (1ull << (g.N & 63)) - 1ull;
+        pc += __popcll(word);
+      }
+      const R v = vec[0];
+      int st = 0;
+      if (zero || v == R(0)) {
+        a.logabs[cfg] = -INFINITY;
+        a.sign[cfg] = 0;
+        st = 5;
+      } else {
+        a.logabs[cfg] = ls + log(fabs((double)v));
+        a.sign[cfg] = v > R(0) ? 1 : -1;
+      }
+      if ((g.N % 2 == 0) && pc != g.N / 2) st = 1;
+      if (a.flags) a.flags[cfg] = st;
+    }
+  }
+}
+
+// Device address of the static scratch, looked up once per device with that
+// device current (the host-side symbol is only a stand-in, not an address).
+static void* g_static_ptr[256];
+static std::mutex g_static_mu;
+
+static cudaError_t static_scratch_ptr(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 256) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_static_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess) return e;
+    g_static_ptr[dev] = p;
+  }
+  *out = g_static_ptr[dev];
+  return cudaSuccess;
+}
+
+template <typename R>
+static peps_status amplitudes_static_impl(const peps_params* p, const void* A_dev, const uint64_t* S_dev, int n,
+                                          double* logabs_dev, int8_t* sign_dev, int32_t* status_dev,
+                                          cudaStream_t stream, char* err, size_t errlen) {
+  Geometry g;
+  g.Lx = p->Lx;
+  g.Ly = p->Ly;
+  g.D = p->D;
+  g.Dc = p->Dc;
+  g.N = p->Lx * p->Ly;
+  g.nwords = (g.N + 63) / 64;
+  g.J1 = p->J1;
+  g.J2 = p->J2;
+  const bool wm = wm_fits_smem(g, sizeof(R));
+  const size_t slot = static_slot_elems(g, wm);
+  const size_t slots = kStaticScratchBytes / (slot * sizeof(R));
+  if (slots < 1) {
+    snprintf(err, errlen,
+             "lattice too large for the allocation-free path: one CTA needs %zu bytes of scratch, the static "
+             "array holds %zu",
+             slot * sizeof(R), kStaticScratchBytes);
+    return PEPS_EINVAL;
+  }
+  void* base = nullptr;
+  cudaError_t e = static_scratch_ptr(&base);
+  if (e != cudaSuccess) {
+    snprintf(err, errlen, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+    return PEPS_ECUDA;
+  }
+  const size_t smem = dyn_smem_bytes(g, sizeof(R), true, wm);
+  e = cudaFuncSetAttribute(k_amplitudes_static<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int dev = 0, nsm = 0, nb = 0;
+  if (e == cudaSuccess) e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_amplitudes_static<R>, kThreads, smem);
+  if (e != cudaSuccess) {
+    snprintf(err, errlen, "launch set-up: %s", cudaGetErrorString(e));
+    return PEPS_ECUDA;
+  }
+  KArgs<R> a;
+  memset(&a, 0, sizeof(a));
+  a.g = g;
+  a.A = (const R*)A_dev;
+  a.S = S_dev;
+  a.n = n;
+  a.logabs = logabs_dev;
+  a.sign = sign_dev;
+  a.flags = status_dev;
+  a.smem_wm = wm ? 1 : 0;
+  long long grid = std::min<long long>((long long)n, (long long)slots);
+  grid = std::min<long long>(grid, (long long)nsm * std::max(nb, 1));
+  k_amplitudes_static<R><<<(int)grid, kThreads, smem, stream>>>(a, (R*)base, slot);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    snprintf(err, errlen, "launch: %s", cudaGetErrorString(e));
+    return PEPS_ECUDA;
+  }
+  return PEPS_OK;
+}
+
+}  // namespace peps
+
+extern "C" peps_status peps_amplitudes_static(const peps_params* p, const void* A_dev, const uint64_t* S_dev,
+                                              int n, double* logabs_dev, int8_t* sign_dev, int32_t* status_dev,
+                                              void* cuda_stream) {
+  char err[256] = {0};
+  if (!p) {
+    peps::set_last_error("null parameters");
+    return PEPS_EINVAL;
+  }
+  if (p->Lx < 2 || p->Ly < 2 || p->Lx > 64 || p->Ly > 64 || (long)p->Lx * p->Ly > 64L * peps::kMaxWords ||
+      p->d != 2 || p->D < 1 || p->D > 16 || p->Dc < 1 || p->Dc > peps::kMaxDc || p->Dc * p->D > peps::kMaxDcD) {
+    peps::set_last_error("parameters out of range (see peps_params)");
+    return PEPS_EINVAL;
+  }
+  if (p->prec != PEPS_FP64 && p->prec != PEPS_FP32) {
+    peps::set_last_error("precision must be PEPS_FP64 or PEPS_FP32");
+    return PEPS_EINVAL;
+  }
+  if (n < 0 || (n > 0 && (!A_dev || !S_dev || !logabs_dev || !sign_dev))) {
+    peps::set_last_error("bad batch size or null pointer");
+    return PEPS_EINVAL;
+  }
+  if (n == 0) return PEPS_OK;
+  const cudaStream_t st = (cudaStream_t)cuda_stream;
+  const peps_status r =
+      p->prec == PEPS_FP64
+          ? peps::amplitudes_static_impl<double>(p, A_dev, S_dev, n, logabs_dev, sign_dev, status_dev, st, err,
+                                                 sizeof(err))
+          : peps::amplitudes_static_impl<float>(p, A_dev, S_dev, n, logabs_dev, sign_dev, status_dev, st, err,
+                                                sizeof(err));
+  if (r != PEPS_OK) peps::set_last_error(err);
+  return r;
+}

@@ -78,6 +78,9 @@ cudaError_t launch_finalize(const Geometry& g, const uint64_t* S, int n, const d
                             int have_eloc, cudaStream_t st);
 cudaError_t launch_grad_finalize(int total, int n_ok_dev_unused, const double* sums, const double* sumO,
                                  const double* sumEO, double* grad, double* cov, cudaStream_t st);
+// Records the calling thread's error message (returned by peps_last_error).
+void set_last_error(const char* msg);
+
 cudaError_t launch_sum_eloc(const double* eloc, const int* status, int n, double* sums, cudaStream_t st);
 
 }  // namespace peps

@@ -61,6 +61,7 @@ def lib():
         "peps_profile_enable": [P, i],
         "peps_profile_read": [P, P, P, i],
         "peps_debug_host_op": [i, i, i, P, P, P, P, P, P],
+        "peps_amplitudes_static": [ctypes.POINTER(Params), P, P, i, P, P, P, P],
         "peps_debug_host_zip": [i, i, i, P, P, P, P, P],
     }
     for name, argt in sigs.items():
@@ -81,7 +82,7 @@ def exported_symbols():
     names = ["peps_create", "peps_destroy", "peps_set_tensors", "peps_amplitudes", "peps_local_energy",
              "peps_log_derivatives", "peps_evaluate", "peps_gradient", "peps_mc_sweep", "peps_synchronize",
              "peps_status_str", "peps_last_error", "peps_debug_host_op", "peps_debug_host_zip",
-             "peps_profile_enable", "peps_profile_read"]
+             "peps_profile_enable", "peps_profile_read", "peps_amplitudes_static"]
     return {n: hasattr(L, n) for n in names}
 
 
@@ -116,6 +117,25 @@ def host_zip(lr, D, Dc, dims, C, M, T, out_shape):
     check(lib().peps_debug_host_zip(int(lr), D, Dc, _ptr(dims), _ptr(_f64(C)), _ptr(_f64(M)), _ptr(_f64(T)),
                                     _ptr(out)))
     return out
+
+
+def amplitudes_static(A_dev, S, Lx, Ly, D, Dc, prec="fp64"):
+    """ln|psi| and sign through the allocation-free entry point.
+
+    ``A_dev`` is a CUDA tensor [N, 2, D^4] (float64 for fp64, float32 for
+    fp32); ``S`` a CUDA int64 tensor [n, ceil(N/64)].  Outputs are allocated
+    here by torch (the caller's memory); the library call itself allocates
+    nothing."""
+    import torch
+    n = S.shape[0]
+    params = Params(Lx, Ly, 2, D, Dc, 1.0, 0.0, PRECISIONS[prec], 0.0)
+    la = torch.empty(n, dtype=torch.float64, device=S.device)
+    sg = torch.empty(n, dtype=torch.int8, device=S.device)
+    st = torch.empty(n, dtype=torch.int32, device=S.device)
+    stream = torch.cuda.current_stream().cuda_stream
+    check(lib().peps_amplitudes_static(ctypes.byref(params), _ptr(A_dev), _ptr(S), n, _ptr(la), _ptr(sg), _ptr(st),
+                                       ctypes.c_void_p(stream)))
+    return la, sg, st
 
 
 class PEPS:
