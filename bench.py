@@ -42,7 +42,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="16x16_D8_Dc16")
-    ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64", "mixed_tf32"])
     ap.add_argument("--n", type=int, default=0, help="batch override (probes only; the metric uses the default)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -233,9 +233,12 @@ def run_ours(args, rank, world, local_rank):
     res = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32" if args.prec == "fp32" else "f64", "data": "synthetic",
+        "dtype": {"fp32": "f32", "fp64": "f64", "mixed_tf32": "tf32/f32"}[args.prec], "data": "synthetic",
         "config": {"workload": args.workload, "lattice": f"{L}x{L}", "D": D, "Dc": Dc, "J2_over_J1": J2,
-                   "configs_per_step_per_gpu": n, "precision_path": f"plain {args.prec.upper()} SIMT",
+                   "configs_per_step_per_gpu": n,
+                   "precision_path": {"fp32": "plain FP32 SIMT", "fp64": "plain FP64 SIMT",
+                                      "mixed_tf32": "two-row transfers on tcgen05 (TF32 in, FP32 accumulate), "
+                                                    "rest FP32 SIMT"}[args.prec],
                    "sampling": "uniform random Sz=0 configurations",
                    "l2": "working set per step (environments, Delta) is tens of GB, far above L2",
                    "parallelism": f"dp{world} (independent configurations)"},

@@ -60,7 +60,8 @@ typedef enum {
 typedef enum {
   PEPS_FP64 = 0,        /* contractions and truncation in FP64 */
   PEPS_FP32 = 1,        /* contractions and truncation in FP32; log scales and reductions FP64 */
-  PEPS_MIXED_TF32 = 2,  /* reserved: tensor-core absorptions */
+  PEPS_MIXED_TF32 = 2,  /* PEPS_FP32 with the two-row sandwich transfers on the tensor cores
+                           (tcgen05, TF32 inputs, FP32 accumulation) where D = 8, Dc = 16 */
   PEPS_MIXED_BF16 = 3   /* reserved: tensor-core absorptions */
 } peps_precision;
 

@@ -136,7 +136,7 @@ def contract_bruteforce(T, Ly: int, Lx: int) -> float:
 
 # -------------------------------------------- boundary MPS (Fig. 1d, Dc)
 
-def absorb_row(mps, Trow, Dc: int, left_to_right: bool):
+def absorb_row(mps, Trow, Dc: int, left_to_right: bool, perturb=None):
     """Absorb one row of the single-layer network into a boundary MPS, truncating to Dc.
 
     ``mps[c]`` is [a, p, b] (left bond, physical index facing the row, right
@@ -149,6 +149,10 @@ def absorb_row(mps, Trow, Dc: int, left_to_right: bool):
     last tensor takes the rest; it is divided by its Frobenius norm n (the
     norm of the whole MPS, since the others are isometries) and ln n is
     returned.  Returns (new_mps, ln n); n == 0 gives ln n = -inf.
+
+    ``perturb`` (diagnostic, default None) is a callable applied to each block
+    X before its SVD; the tests use it to measure how strongly the truncated
+    result reacts to rounding-sized changes of X (conditioning of the cut).
     """
     L = len(Trow)
     out = [None] * L
@@ -159,6 +163,8 @@ def absorb_row(mps, Trow, Dc: int, left_to_right: bool):
             X = np.tensordot(Y, Trow[c], axes=([1, 2], [0, 2]))   # [k, b, r, o]
             X = X.transpose(0, 3, 1, 2)                           # [k, o, b, r]
             k, o, b, rr = X.shape
+            if perturb is not None:
+                X = perturb(X)
             if c < L - 1:
                 U, s, Vt = np.linalg.svd(X.reshape(k * o, b * rr), full_matrices=False)
                 K = min(Dc, k * o, b * rr)
@@ -174,6 +180,8 @@ def absorb_row(mps, Trow, Dc: int, left_to_right: bool):
             X = np.tensordot(Y, Trow[c], axes=([1, 2], [2, 1]))   # [a, k, l, o]
             X = X.transpose(0, 2, 3, 1)                           # [a, l, o, k]
             a, l, o, k = X.shape
+            if perturb is not None:
+                X = perturb(X)
             if c > 0:
                 U, s, Vt = np.linalg.svd(X.reshape(a * l, o * k), full_matrices=False)
                 K = min(Dc, a * l, o * k)
@@ -193,7 +201,7 @@ def trivial_mps(L: int):
     return [np.ones((1, 1, 1)) for _ in range(L)]
 
 
-def top_envs(T, Ly: int, Lx: int, Dc: int):
+def top_envs(T, Ly: int, Lx: int, Dc: int, perturb=None):
     """Upper environments U_r (rows 0..r absorbed), r = -1..Ly-1, as a list indexed r+1.
 
     Row r is absorbed left-to-right when r is even, right-to-left when odd.
@@ -204,7 +212,7 @@ def top_envs(T, Ly: int, Lx: int, Dc: int):
     envs = [(trivial_mps(Lx), 0.0)]
     mps, ls = envs[0]
     for r in range(Ly):
-        mps, ln = absorb_row(mps, rows[r], Dc, left_to_right=(r % 2 == 0))
+        mps, ln = absorb_row(mps, rows[r], Dc, left_to_right=(r % 2 == 0), perturb=perturb)
         ls += ln
         envs.append((mps, ls))
         if ln == -math.inf:
@@ -214,7 +222,7 @@ def top_envs(T, Ly: int, Lx: int, Dc: int):
     return envs
 
 
-def bottom_envs(T, Ly: int, Lx: int, Dc: int):
+def bottom_envs(T, Ly: int, Lx: int, Dc: int, perturb=None):
     """Lower environments L_r (rows r..Ly-1 absorbed), r = Ly..0, as a list indexed r.
 
     Built from the bottom: the j-th absorbed row (j = Ly-1-r) goes
@@ -228,7 +236,7 @@ def bottom_envs(T, Ly: int, Lx: int, Dc: int):
     for r in reversed(range(Ly)):
         j = Ly - 1 - r
         flipped = [t.transpose(0, 1, 3, 2) for t in rows[r]]
-        mps, ln = absorb_row(mps, flipped, Dc, left_to_right=(j % 2 == 0))
+        mps, ln = absorb_row(mps, flipped, Dc, left_to_right=(j % 2 == 0), perturb=perturb)
         ls += ln
         envs[r] = (mps, ls)
         if ln == -math.inf:
@@ -322,7 +330,7 @@ class Evaluation:
 PEPS_OK, PEPS_EINVAL, PEPS_ENUMERIC = 0, 1, 5
 
 
-def evaluate(A, spins, Ly, Lx, Dc, J1, J2, want_O=True):
+def evaluate(A, spins, Ly, Lx, Dc, J1, J2, want_O=True, perturb=None):
     """ln|psi|, sign, E_loc (Sec. II, E(S)) and Delta = B/W (Sec. II) for one configuration.
 
     Ratios W(S')/W(S) and Delta reuse the environments of S: a pair inside
@@ -338,8 +346,8 @@ def evaluate(A, spins, Ly, Lx, Dc, J1, J2, want_O=True):
         return ev
     D = A.shape[2]
     T = project(A, spins, Ly, Lx)
-    up = top_envs(T, Ly, Lx, Dc)
-    dn = bottom_envs(T, Ly, Lx, Dc)
+    up = top_envs(T, Ly, Lx, Dc, perturb)
+    dn = bottom_envs(T, Ly, Lx, Dc, perturb)
     mps, ls = up[Ly]
     v = close_chain(mps) if ls != -math.inf else 0.0
     if v == 0.0:

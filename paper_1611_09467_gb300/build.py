@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT, "libpeps.so")
 SOURCES = ["kernels.cu", "api.cu"]
-HEADERS = ["contract.cuh", "device.cuh", "kernels.h", "pair_fused.cuh", os.path.join("..", "..", "include", "peps.h")]
+HEADERS = ["contract.cuh", "device.cuh", "kernels.h", "pair_fused.cuh", "pair_tc.cuh", os.path.join("..", "..", "include", "peps.h")]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]

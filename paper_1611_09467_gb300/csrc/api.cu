@@ -108,10 +108,11 @@ struct peps_ctx {
   int nslots = 0;
   size_t elem = 8;
   bool wm_smem = false;
-  DevBuf A, triv_mps, triv_t1, triv_t2, bd;
+  DevBuf A, triv_mps, triv_t1, triv_t2, bd, tcB;
   DevBuf env, small, O, scratch, gsum;
   int chunk = 0;  // configurations per pass
   int res_boundary = 0, res_row = 0, res_pair = 0, res_mc = 0;  // resident CTAs per kernel
+  bool pair_tc = false;  // two-row step on the tensor cores (PEPS_MIXED_TF32, D = 8, Dc = 16)
   // profiling: event pairs per kernel id
   bool prof = false;
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev;
@@ -153,6 +154,50 @@ peps_status upload_tensors(peps_ctx* c, const double* A_host) {
   PEPS_CUDA(c->A.ensure(nel * sizeof(R)));
   PEPS_CUDA(cudaMemcpyAsync(c->A.p, h.data(), nel * sizeof(R), cudaMemcpyHostToDevice, c->stream));
   PEPS_CUDA(cudaStreamSynchronize(c->stream));
+  return PEPS_OK;
+}
+
+// TF32 rounding to nearest, ties away from zero (the rounding of cvt.rna.tf32.f32).
+float tf32_rna(float x) {
+  uint32_t b;
+  std::memcpy(&b, &x, 4);
+  if ((b & 0x7F800000u) != 0x7F800000u) b = (b + 0x1000u) & 0xFFFFE000u;
+  float r;
+  std::memcpy(&r, &b, 4);
+  return r;
+}
+
+// Site tensors as the B tiles of the tensor-core two-row step (pair_tc.cuh):
+// per (direction, site, spin) TA[n=(yout,d)][k=(u,yin)] and TB[n=(yout,d)][k=(yin,u)],
+// core-matrix layout, TF32-rounded.
+peps_status setup_tc_tiles(peps_ctx* c, const double* A_host) {
+  const int N = c->g.N, D = 8;
+  const size_t tile = kTcTile, per = 2 * tile;
+  std::vector<float> h((size_t)2 * N * 2 * per, 0.f);
+  auto kmaj = [](int row, int k, int K) { return (row >> 3) * (K >> 2) * 32 + (k >> 2) * 32 + (row & 7) * 4 + (k & 3); };
+  for (int dir = 0; dir < 2; ++dir)
+    for (int i = 0; i < N; ++i)
+      for (int sp = 0; sp < 2; ++sp) {
+        float* TA = h.data() + ((size_t)(dir * N + i) * 2 + sp) * per;
+        float* TB = TA + tile;
+        const double* Ai = A_host + ((size_t)i * 2 + sp) * 4096;
+        for (int n = 0; n < 64; ++n)
+          for (int k = 0; k < 64; ++k) {
+            const int yout = n >> 3, d = n & 7;
+            {
+              const int u = k >> 3, yin = k & 7;
+              const int l = dir == 0 ? yin : yout, r = dir == 0 ? yout : yin;
+              TA[kmaj(n, k, 64)] = tf32_rna((float)Ai[l * 512 + r * 64 + u * D + d]);
+            }
+            {
+              const int yin = k >> 3, u = k & 7;
+              const int l = dir == 0 ? yin : yout, r = dir == 0 ? yout : yin;
+              TB[kmaj(n, k, 64)] = tf32_rna((float)Ai[l * 512 + r * 64 + u * D + d]);
+            }
+          }
+      }
+  PEPS_CUDA(c->tcB.ensure(h.size() * sizeof(float)));
+  PEPS_CUDA(cudaMemcpy(c->tcB.p, h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice));
   return PEPS_OK;
 }
 
@@ -259,6 +304,7 @@ KArgs<R> make_args(peps_ctx* c, const uint64_t* S, int n, const Small& sm) {
   a.scratch = (R*)c->scratch.p;
   a.slot_elems = slot_elems(c);
   a.smem_wm = c->wm_smem ? 1 : 0;
+  a.tcB = (const float*)c->tcB.p;
   return a;
 }
 
@@ -283,7 +329,15 @@ peps_status evaluate_chunk(peps_ctx* c, const uint64_t* S, int n, bool need_env_
   if (need_pairs && c->g.Ly > 1) {
     grid = std::min(n * (c->g.Ly - 1), std::min(c->nslots, c->res_pair));
     Prof pf(c, 2);
-    PEPS_CUDA(launch_pair<R>(a, std::max(grid, 1), c->stream));
+    if constexpr (sizeof(R) == 4) {
+      if (c->pair_tc) {
+        PEPS_CUDA(launch_pair_tc(a, std::max(grid, 1), c->stream));
+      } else {
+        PEPS_CUDA(launch_pair<R>(a, std::max(grid, 1), c->stream));
+      }
+    } else {
+      PEPS_CUDA(launch_pair<R>(a, std::max(grid, 1), c->stream));
+    }
   } else {
     PEPS_CUDA(cudaMemsetAsync(sm.eloc_v, 0, (size_t)n * c->g.Ly * sizeof(double), c->stream));
   }
@@ -424,8 +478,8 @@ peps_status peps_create(const peps_params* p, const double* A_host, void* stream
   if (p->d != 2) return fail(PEPS_EINVAL, "d must be 2");
   if (p->D < 1 || p->D > 16) return fail(PEPS_EINVAL, "D must be in [1, 16]");
   if (p->Dc < 1 || p->Dc > kMaxDc || p->Dc * p->D > kMaxDcD) return fail(PEPS_EINVAL, "need 1 <= Dc <= 32, Dc*D <= 256");
-  if (p->prec != PEPS_FP64 && p->prec != PEPS_FP32)
-    return fail(PEPS_EINVAL, "precision not available: use PEPS_FP64 or PEPS_FP32");
+  if (p->prec != PEPS_FP64 && p->prec != PEPS_FP32 && p->prec != PEPS_MIXED_TF32)
+    return fail(PEPS_EINVAL, "precision not available: use PEPS_FP64, PEPS_FP32 or PEPS_MIXED_TF32");
   if (!std::isfinite(p->J1) || !std::isfinite(p->J2)) return fail(PEPS_EINVAL, "non-finite coupling");
   // padded entries must be zero (open edges of dimension one, Eq. 1)
   const int D = p->D, Lx = p->Lx, Ly = p->Ly, N = Lx * Ly;
@@ -471,13 +525,15 @@ peps_status peps_create(const peps_params* p, const double* A_host, void* stream
   } else {
     c->res_boundary = max_blocks_boundary<float>(c->g);
     c->res_row = max_blocks_row<float>(c->g);
-    c->res_pair = max_blocks_pair_fused<float>(c->g);
+    c->pair_tc = p->prec == PEPS_MIXED_TF32 && c->g.D == 8 && c->g.Dc == 16;
+    c->res_pair = c->pair_tc ? max_blocks_pair_tc() : max_blocks_pair_fused<float>(c->g);
     if (!c->res_pair) c->res_pair = max_blocks_pair<float>(c->g);
     c->res_mc = max_blocks_mc<float>(c->g);
   }
   c->nslots = std::max(std::max(c->res_boundary, c->res_row), std::max(c->res_pair, c->res_mc));
   peps_status st = c->elem == 8 ? upload_tensors<double>(c, A_host) : upload_tensors<float>(c, A_host);
   if (st == PEPS_OK) st = c->elem == 8 ? setup_trivial<double>(c) : setup_trivial<float>(c);
+  if (st == PEPS_OK && c->pair_tc) st = setup_tc_tiles(c, A_host);
   if (st != PEPS_OK) {
     peps_destroy(c);
     return st;
@@ -494,7 +550,7 @@ peps_status peps_destroy(peps_ctx* c) {
     cudaEventDestroy(e.second.first);
     cudaEventDestroy(e.second.second);
   }
-  DevBuf* bufs[] = {&c->A, &c->triv_mps, &c->triv_t1, &c->triv_t2, &c->bd, &c->env, &c->small, &c->O, &c->scratch, &c->gsum};
+  DevBuf* bufs[] = {&c->tcB, &c->A, &c->triv_mps, &c->triv_t1, &c->triv_t2, &c->bd, &c->env, &c->small, &c->O, &c->scratch, &c->gsum};
   for (DevBuf* b : bufs) b->release();
   delete c;
   return PEPS_OK;
@@ -502,7 +558,9 @@ peps_status peps_destroy(peps_ctx* c) {
 
 peps_status peps_set_tensors(peps_ctx* c, const double* A_host) {
   if (!c || !A_host) return fail(PEPS_EINVAL, "null argument");
-  return c->elem == 8 ? upload_tensors<double>(c, A_host) : upload_tensors<float>(c, A_host);
+  peps_status st = c->elem == 8 ? upload_tensors<double>(c, A_host) : upload_tensors<float>(c, A_host);
+  if (st == PEPS_OK && c->pair_tc) st = setup_tc_tiles(c, A_host);
+  return st;
 }
 
 peps_status peps_evaluate(peps_ctx* c, const uint64_t* S, int n, double* logabs, int8_t* sign, double* eloc, void* O,

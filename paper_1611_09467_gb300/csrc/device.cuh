@@ -310,83 +310,108 @@ __device__ int sturm_count(const R* t2, int n2, R x, R pivmin) {
 // Inverse iteration for one eigenvalue of the n2 x n2 zero-diagonal
 // symmetric tridiagonal with off-diagonal t: Gaussian elimination with
 // partial pivoting on (T - lam I), two solves from a fixed pseudo-random
-// start vector.  Sequential, one thread per eigenvalue; the workspace is
-// interleaved across the K threads (element i of thread k at i * K + k) so
-// the lock-step accesses of a warp are contiguous.
+// start vector.  Sequential, one thread per eigenvalue.  The recurrences
+// carry their running values in registers; memory only receives the factors
+// and reads back values that do not depend on the running recurrence, so
+// loads can be issued ahead.  The workspace is interleaved across the K
+// threads (element i of thread k at i * K + k): lock-step accesses of a warp
+// are contiguous.
 template <typename R>
 __device__ void inverse_iteration(const R* t, int n2, R lam, R pivtiny, R* ws, int K, int k, R* z, int zs,
                                   unsigned seed) {
   const size_t st = (size_t)n2 * K;
-  R* dd = ws + k;
-  R* du = dd + st;
-  R* du2 = du + st;
-  R* mult = du2 + st;
-  R* piv = mult + st;
-  R* b = piv + st;
+  R* rdd = ws + k;       // reciprocal pivots of U
+  R* du = rdd + st;      // first super-diagonal of U
+  R* du2 = du + st;      // second super-diagonal of U
+  R* mult = du2 + st;    // multipliers of L
+  R* piv = mult + st;    // 1 where rows i, i+1 were interchanged
+  R* b = piv + st;       // right-hand side / solution
 #define IX(i) ((size_t)(i) * K)
-  for (int i = 0; i < n2; ++i) {
-    dd[IX(i)] = -lam;
-    du[IX(i)] = i < n2 - 1 ? t[i] : R(0);
-    du2[IX(i)] = R(0);
-  }
+  // ---- factorisation, carrying dd[i], du[i] (current row) and dd[i+1], du[i+1]
+  R cur_d = -lam, cur_u = n2 > 1 ? t[0] : R(0);
   for (int i = 0; i < n2 - 1; ++i) {
     const R sub = t[i];
-    R a = dd[IX(i)];
-    if (fabs(a) >= fabs(sub)) {
-      if (a == R(0)) a = dd[IX(i)] = pivtiny;
-      const R l = sub / a;
-      mult[IX(i)] = l;
+    R next_d = -lam;
+    R next_u = i + 1 < n2 - 1 ? t[i + 1] : R(0);
+    R d_i, u_i, u2_i, l;
+    if (fabs(cur_d) >= fabs(sub)) {
+      d_i = cur_d == R(0) ? pivtiny : cur_d;
+      l = sub / d_i;
+      u_i = cur_u;
+      u2_i = R(0);
+      next_d -= l * cur_u;
       piv[IX(i)] = R(0);
-      dd[IX(i + 1)] -= l * du[IX(i)];
     } else {
-      const R l = a / sub;
-      mult[IX(i)] = l;
+      l = cur_d / sub;
+      d_i = sub;
+      u_i = next_d;
+      next_d = cur_u - l * next_d;
+      u2_i = next_u;
+      next_u = -l * next_u;
       piv[IX(i)] = R(1);
-      dd[IX(i)] = sub;
-      const R tmp = du[IX(i)];
-      du[IX(i)] = dd[IX(i + 1)];
-      dd[IX(i + 1)] = tmp - l * dd[IX(i + 1)];
-      if (i < n2 - 2) {
-        du2[IX(i)] = du[IX(i + 1)];
-        du[IX(i + 1)] = -l * du[IX(i + 1)];
-      }
     }
+    if (fabs(d_i) < pivtiny) d_i = d_i < R(0) ? -pivtiny : pivtiny;
+    rdd[IX(i)] = R(1) / d_i;
+    du[IX(i)] = u_i;
+    du2[IX(i)] = u2_i;
+    mult[IX(i)] = l;
+    cur_d = next_d;
+    cur_u = next_u;
   }
-  for (int i = 0; i < n2; ++i) {
-    R v = dd[IX(i)];
-    if (fabs(v) < pivtiny) v = v < R(0) ? -pivtiny : pivtiny;
-    dd[IX(i)] = R(1) / v;   // stored as reciprocals for the solves
-  }
+  if (fabs(cur_d) < pivtiny) cur_d = cur_d < R(0) ? -pivtiny : pivtiny;
+  rdd[IX(n2 - 1)] = R(1) / cur_d;
+  du[IX(n2 - 1)] = R(0);
+  du2[IX(n2 - 1)] = R(0);
   unsigned h = seed * 2654435761u + 12345u;
-  for (int i = 0; i < n2; ++i) {
-    h ^= h << 13; h ^= h >> 17; h ^= h << 5;
-    b[IX(i)] = R((int)(h & 0xffffu) - 32768) / R(32768) + R(0.001);
-  }
   for (int it = 0; it < 2; ++it) {
+    // ---- forward: apply the row interchanges and L^-1, carrying b[i]
+    R bi;
+    if (it == 0) {
+      h ^= h << 13; h ^= h >> 17; h ^= h << 5;
+      bi = R((int)(h & 0xffffu) - 32768) / R(32768) + R(0.001);
+    } else {
+      bi = b[IX(0)];
+    }
+#pragma unroll 4
     for (int i = 0; i < n2 - 1; ++i) {
-      if (piv[IX(i)] == R(0)) {
-        b[IX(i + 1)] -= mult[IX(i)] * b[IX(i)];
+      R bn;
+      if (it == 0) {
+        h ^= h << 13; h ^= h >> 17; h ^= h << 5;
+        bn = R((int)(h & 0xffffu) - 32768) / R(32768) + R(0.001);
       } else {
-        const R tmp = b[IX(i)];
-        b[IX(i)] = b[IX(i + 1)];
-        b[IX(i + 1)] = tmp - mult[IX(i)] * b[IX(i)];
+        bn = b[IX(i + 1)];
+      }
+      const R l = mult[IX(i)];
+      if (piv[IX(i)] == R(0)) {
+        b[IX(i)] = bi;
+        bi = bn - l * bi;
+      } else {
+        b[IX(i)] = bn;
+        bi = bi - l * bn;
       }
     }
-    b[IX(n2 - 1)] *= dd[IX(n2 - 1)];
-    if (n2 >= 2) b[IX(n2 - 2)] = (b[IX(n2 - 2)] - du[IX(n2 - 2)] * b[IX(n2 - 1)]) * dd[IX(n2 - 2)];
-    for (int i = n2 - 3; i >= 0; --i)
-      b[IX(i)] = (b[IX(i)] - du[IX(i)] * b[IX(i + 1)] - du2[IX(i)] * b[IX(i + 2)]) * dd[IX(i)];
-    R mx = R(0);
-    for (int i = 0; i < n2; ++i) mx = fmax(mx, fabs(b[IX(i)]));
+    b[IX(n2 - 1)] = bi;
+    // ---- backward: U^-1, carrying y[i+1], y[i+2]; track max |y|
+    R y1 = R(0), y2 = R(0), mx = R(0);
+#pragma unroll 4
+    for (int i = n2 - 1; i >= 0; --i) {
+      const R y = (b[IX(i)] - du[IX(i)] * y1 - du2[IX(i)] * y2) * rdd[IX(i)];
+      b[IX(i)] = y;
+      mx = fmax(mx, fabs(y));
+      y2 = y1;
+      y1 = y;
+    }
+    // ---- normalise (scale by the max first: the solve can amplify by 1/pivtiny)
     if (!(mx > R(0))) mx = R(1);
     const R imx = R(1) / mx;
     R ss = R(0);
+#pragma unroll 4
     for (int i = 0; i < n2; ++i) {
       const R v = b[IX(i)] * imx;
-      b[IX(i)] = v;
       ss += v * v;
     }
-    const R inv = R(1) / dsqrt(ss);
+    const R inv = imx / dsqrt(ss);
+#pragma unroll 4
     for (int i = 0; i < n2; ++i) b[IX(i)] *= inv;
   }
   for (int i = 0; i < n2; ++i) z[(size_t)i * zs] = b[IX(i)];

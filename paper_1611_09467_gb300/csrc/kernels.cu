@@ -27,6 +27,7 @@
 #include "device.cuh"
 #include "kernels.h"
 #include "pair_fused.cuh"
+#include "pair_tc.cuh"
 
 namespace peps {
 
@@ -48,6 +49,16 @@ __device__ __forceinline__ TDims tdims(const Geometry& g, int row, int col) {
   t.u = row == 0 ? 1 : g.D;
   t.d = row == g.Ly - 1 ? 1 : g.D;
   return t;
+}
+
+// Kernels with large shared-memory footprints ask for the maximum carve-out so
+// the occupancy the grids are sized for is the one the hardware grants.
+template <typename F>
+static cudaError_t prefer_shared(F* f, size_t smem) {
+  cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+  return e;
 }
 
 // ---------------------------------------------------------------- layouts
@@ -574,6 +585,125 @@ __global__ void __launch_bounds__(kThreads) k_pair_fused(KArgs<R> a) {
   }
 }
 
+// ------------------------------------------------------------ k_pair_tc
+// k_pair_fused with the tensor-core step (pair_tc.cuh), D = 8, Dc = 16, TF32
+// inputs with FP32 accumulation.  Each CTA holds kTmemCols TMEM columns for
+// its lifetime; a timed-out wait marks the configuration and ends the CTA
+// after releasing TMEM.
+__global__ void __launch_bounds__(kThreads) k_pair_tc(KArgs<float> a) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  __shared__ float red[64];
+  __shared__ uint64_t sp[kMaxWords];
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ __align__(8) uint64_t tbar;
+  __shared__ uint32_t tmem_holder;
+  constexpr int D = 8, Dc = 16;
+  float* sm = reinterpret_cast<float*>(smem_raw);
+  const Geometry& g = a.g;
+  const int Lx = g.Lx, Ly = g.Ly;
+  constexpr int envT = Dc * D * Dc, envT2 = Dc * D * D * Dc;
+  float* p = a.scratch + (size_t)blockIdx.x * a.slot_elems;
+  float* Hb = p; p += (size_t)(Lx + 1) * envT2;
+  float* E0 = p; p += envT2;
+  float* E1 = p; p += envT2;
+  float* X1 = p;
+  if ((threadIdx.x >> 5) == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc::smem_u32(&tmem_holder)),
+                 "r"(tc::kTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(tc::smem_u32(&mbar)), "r"(1));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(tc::smem_u32(&tbar)), "r"(1));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  PairTc st;
+  st.tmem = tmem_holder;
+  st.mbar = &mbar;
+  st.tbar = &tbar;
+  st.phase = 0;
+  st.tphase = 0;
+  st.ok = true;
+  // B tiles of site i, spin s, direction dir (0 left, 1 right): TA at +0, TB at +kTcTile
+  auto tile = [&](int dir, int i, int sp_) { return a.tcB + ((size_t)(dir * g.N + i) * 2 + sp_) * 2 * kTcTile; };
+  const int npairs = Ly - 1;
+  for (int item = blockIdx.x; item < a.n * npairs && st.ok; item += gridDim.x) {
+    const int cfg = item / npairs, r = item % npairs;
+    __syncthreads();
+    for (int i = threadIdx.x; i < g.nwords; i += blockDim.x) sp[i] = a.S[(size_t)cfg * g.nwords + i];
+    for (int e = threadIdx.x; e < envT2; e += blockDim.x) Hb[(size_t)Lx * envT2 + e] = a.triv_t2[e];
+    __syncthreads();
+    const float* Mu = r == 0 ? a.triv_mps : a.envU + ((size_t)cfg * Ly + (r - 1)) * Lx * envT;
+    const float* Md = r + 2 > Ly - 1 ? a.triv_mps : a.envL + ((size_t)cfg * Ly + (r + 2)) * Lx * envT;
+    for (int c = Lx - 1; c >= 0; --c) {
+      const int s1 = r * Lx + c, s2 = (r + 1) * Lx + c;
+      pair_step_tc(st, true, Hb + (size_t)(c + 1) * envT2, Hb + (size_t)c * envT2, Mu + (size_t)c * envT,
+                   tile(1, s1, spin_of(sp, s1)), tile(1, s2, spin_of(sp, s2)) + kTcTile, Md + (size_t)c * envT,
+                   nullptr, sm, red);
+    }
+    __syncthreads();
+    const float W = Hb[0];
+    const bool ok = W != 0.f;
+    double ev = 0.0;
+    const float* E = a.triv_t2;
+    float* En = E0;
+    for (int c = 0; c < Lx; ++c) {
+      const int i1 = r * Lx + c, i2 = (r + 1) * Lx + c;
+      const int a1 = spin_of(sp, i1), a2 = spin_of(sp, i2);
+      const float* Muc = Mu + (size_t)c * envT;
+      const float* Mdc = Md + (size_t)c * envT;
+      if (a1 != a2) {
+        const float wp = pair_step_tc(st, false, E, nullptr, Muc, tile(0, i1, a2), tile(0, i2, a1) + kTcTile, Mdc,
+                                      Hb + (size_t)(c + 1) * envT2, sm, red);
+        if (ok) ev += 0.5 * g.J1 * ((double)wp / (double)W);
+      }
+      if (c < Lx - 1 && g.J2 != 0.0) {
+        const int j1 = i1 + 1, j2 = i2 + 1;
+        const int b1 = spin_of(sp, j1), b2 = spin_of(sp, j2);
+        const float* Mun = Mu + (size_t)(c + 1) * envT;
+        const float* Mdn = Md + (size_t)(c + 1) * envT;
+        if (a1 != b2) {
+          pair_step_tc(st, false, E, X1, Muc, tile(0, i1, b2), tile(0, i2, a2) + kTcTile, Mdc, nullptr, sm, red);
+          __syncthreads();
+          const float wp = pair_step_tc(st, false, X1, nullptr, Mun, tile(0, j1, b1), tile(0, j2, a1) + kTcTile, Mdn,
+                                        Hb + (size_t)(c + 2) * envT2, sm, red);
+          if (ok) ev += 0.5 * g.J2 * ((double)wp / (double)W);
+        }
+        if (b1 != a2) {
+          pair_step_tc(st, false, E, X1, Muc, tile(0, i1, a1), tile(0, i2, b1) + kTcTile, Mdc, nullptr, sm, red);
+          __syncthreads();
+          const float wp = pair_step_tc(st, false, X1, nullptr, Mun, tile(0, j1, a2), tile(0, j2, b2) + kTcTile, Mdn,
+                                        Hb + (size_t)(c + 2) * envT2, sm, red);
+          if (ok) ev += 0.5 * g.J2 * ((double)wp / (double)W);
+        }
+      }
+      if (c < Lx - 1) {
+        pair_step_tc(st, false, E, En, Muc, tile(0, i1, a1), tile(0, i2, a2) + kTcTile, Mdc, nullptr, sm, red);
+        __syncthreads();
+        E = En;
+        En = (En == E0) ? E1 : E0;
+      }
+    }
+    if (threadIdx.x == 0) {
+      a.eloc_v[(size_t)cfg * Ly + r] = ev;
+      if (!ok) atomicOr(&a.flags[cfg], kFlagZeroW);
+      if (!st.ok) atomicOr(&a.flags[cfg], kFlagTimeout);
+    }
+  }
+  if (!st.ok && threadIdx.x == 0) {
+    // configurations this CTA did not reach are marked too
+    for (int item = blockIdx.x; item < a.n * npairs; item += gridDim.x) atomicOr(&a.flags[item / npairs], kFlagTimeout);
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  if ((threadIdx.x >> 5) == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_holder), "r"(tc::kTmemCols));
+}
+
 // ------------------------------------------------------------ k_finalize
 // E(S) = sum over bonds of J (+1/4 parallel, -1/4 antiparallel) plus the
 // exchange terms already summed per row / row pair.  Status: S^z != 0 ->
@@ -591,6 +721,7 @@ __global__ void k_finalize(Geometry g, const uint64_t* S, int n, const double* e
   }
   int st = 0;
   if ((g.N % 2 == 0) && pc != g.N / 2) st = 1;
+  else if (flags[cfg] & kFlagTimeout) st = 4;
   else if (flags[cfg] & kFlagZeroW) st = 5;
   if (status) status[cfg] = st;
   if (!have_eloc || eloc == nullptr) return;
@@ -844,7 +975,7 @@ int max_blocks_boundary(const Geometry& g) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   const size_t smem = dyn_smem_bytes(g, sizeof(R), true, wm_fits_smem(g, sizeof(R)));
-  cudaFuncSetAttribute(k_boundary<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  prefer_shared(k_boundary<R>, smem);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_boundary<R>, kThreads, smem);
   if (nb < 1) nb = 1;
   return nsm * nb;
@@ -853,7 +984,7 @@ int max_blocks_boundary(const Geometry& g) {
 template <typename R>
 cudaError_t launch_boundary(const KArgs<R>& a, int dirs, int grid, cudaStream_t st) {
   const size_t smem = dyn_smem_bytes(a.g, sizeof(R), true, a.smem_wm != 0);
-  cudaError_t e = cudaFuncSetAttribute(k_boundary<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = prefer_shared(k_boundary<R>, smem);
   if (e != cudaSuccess) return e;
   k_boundary<R><<<grid, kThreads, smem, st>>>(a, dirs);
   return cudaGetLastError();
@@ -865,7 +996,7 @@ int max_blocks_mc(const Geometry& g) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   const size_t smem = dyn_smem_bytes(g, sizeof(R), true, wm_fits_smem(g, sizeof(R)));
-  cudaFuncSetAttribute(k_mc<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  prefer_shared(k_mc<R>, smem);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_mc<R>, kThreads, smem);
   if (nb < 1) nb = 1;
   return nsm * nb;
@@ -875,7 +1006,7 @@ template <typename R>
 cudaError_t launch_mc(const KArgs<R>& a, uint64_t* S, int nsweeps, uint64_t seed, uint64_t chain0, uint64_t sweep0,
                       long long* accepted, int grid, cudaStream_t st) {
   const size_t smem = dyn_smem_bytes(a.g, sizeof(R), true, a.smem_wm != 0);
-  cudaError_t e = cudaFuncSetAttribute(k_mc<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = prefer_shared(k_mc<R>, smem);
   if (e != cudaSuccess) return e;
   k_mc<R><<<grid, kThreads, smem, st>>>(a, S, nsweeps, seed, chain0, sweep0, accepted);
   return cudaGetLastError();
@@ -887,7 +1018,7 @@ int max_blocks_row(const Geometry& g) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   const size_t smem = dyn_smem_bytes(g, sizeof(R), false, false);
-  cudaFuncSetAttribute(k_row<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  prefer_shared(k_row<R>, smem);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_row<R>, kThreads, smem);
   return nsm * (nb < 1 ? 1 : nb);
 }
@@ -898,7 +1029,7 @@ int max_blocks_pair(const Geometry& g) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   const size_t smem = dyn_smem_bytes(g, sizeof(R), false, false);
-  cudaFuncSetAttribute(k_pair<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  prefer_shared(k_pair<R>, smem);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pair<R>, kThreads, smem);
   return nsm * (nb < 1 ? 1 : nb);
 }
@@ -906,7 +1037,7 @@ int max_blocks_pair(const Geometry& g) {
 template <typename R>
 cudaError_t launch_row(const KArgs<R>& a, int grid, cudaStream_t st) {
   const size_t smem = dyn_smem_bytes(a.g, sizeof(R), false, false);
-  cudaError_t e = cudaFuncSetAttribute(k_row<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = prefer_shared(k_row<R>, smem);
   if (e != cudaSuccess) return e;
   k_row<R><<<grid, kThreads, smem, st>>>(a);
   return cudaGetLastError();
@@ -915,7 +1046,7 @@ cudaError_t launch_row(const KArgs<R>& a, int grid, cudaStream_t st) {
 template <typename R, int D, int Dc>
 static cudaError_t launch_pair_fused(const KArgs<R>& a, int grid, cudaStream_t st) {
   const size_t smem = (size_t)PairSmem<D, Dc>::total * sizeof(R);
-  cudaError_t e = cudaFuncSetAttribute(k_pair_fused<R, D, Dc>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = prefer_shared(k_pair_fused<R, D, Dc>, smem);
   if (e != cudaSuccess) return e;
   k_pair_fused<R, D, Dc><<<grid, kThreads, smem, st>>>(a);
   return cudaGetLastError();
@@ -927,7 +1058,7 @@ static int fused_blocks() {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   const size_t smem = (size_t)PairSmem<D, Dc>::total * sizeof(R);
-  cudaFuncSetAttribute(k_pair_fused<R, D, Dc>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  prefer_shared(k_pair_fused<R, D, Dc>, smem);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pair_fused<R, D, Dc>, kThreads, smem);
   return nsm * (nb < 1 ? 1 : nb);
 }
@@ -953,6 +1084,29 @@ int max_blocks_pair_fused(const Geometry& g) {
   return 0;
 }
 
+int max_blocks_pair_tc() {
+  int dev = 0, nsm = 0, nb = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const size_t smem = (size_t)PairTcSmem::total * sizeof(float) + 1024;
+  prefer_shared(k_pair_tc, smem);
+  cudaFuncSetAttribute(k_pair_tc, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pair_tc, kThreads, smem);
+  // each resident CTA holds kTmemCols of the SM's 512 TMEM columns
+  nb = std::min(nb, 512 / tc::kTmemCols);
+  return nsm * (nb < 1 ? 1 : nb);
+}
+
+cudaError_t launch_pair_tc(const KArgs<float>& a, int grid, cudaStream_t st) {
+  const size_t smem = (size_t)PairTcSmem::total * sizeof(float) + 1024;
+  cudaError_t e = prefer_shared(k_pair_tc, smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_pair_tc, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+  if (e != cudaSuccess) return e;
+  k_pair_tc<<<grid, kThreads, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
 template <typename R>
 cudaError_t launch_pair(const KArgs<R>& a, int grid, cudaStream_t st) {
   switch (pair_fused_id<R>(a.g)) {
@@ -962,7 +1116,7 @@ cudaError_t launch_pair(const KArgs<R>& a, int grid, cudaStream_t st) {
     case 4: return launch_pair_fused<R, sizeof(R) == 4 ? 8 : 2, sizeof(R) == 4 ? 16 : 4>(a, grid, st);
   }
   const size_t smem = dyn_smem_bytes(a.g, sizeof(R), false, false);
-  cudaError_t e = cudaFuncSetAttribute(k_pair<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = prefer_shared(k_pair<R>, smem);
   if (e != cudaSuccess) return e;
   k_pair<R><<<grid, kThreads, smem, st>>>(a);
   return cudaGetLastError();
@@ -1185,7 +1339,7 @@ static peps_status amplitudes_static_impl(const peps_params* p, const void* A_de
     return PEPS_ECUDA;
   }
   const size_t smem = dyn_smem_bytes(g, sizeof(R), true, wm);
-  e = cudaFuncSetAttribute(k_amplitudes_static<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  e = prefer_shared(k_amplitudes_static<R>, smem);
   int dev = 0, nsm = 0, nb = 0;
   if (e == cudaSuccess) e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);

@@ -11,8 +11,12 @@ constexpr int kMaxWords = 64;        // up to 4096 sites
 constexpr int kMaxDc = 32;           // K <= 32 in the truncation
 constexpr int kMaxDcD = 256;         // Dc * D <= 256
 
+// Floats per pre-arranged B tile of the tensor-core two-row step.
+constexpr int kTcTile = 4096;
+
 // Per-configuration status bits written by the kernels.
 constexpr int kFlagZeroW = 1;        // some W (psi, a row or a row pair) is exactly zero
+constexpr int kFlagTimeout = 2;      // a bounded device wait gave up
 
 struct Geometry {
   int Lx, Ly, D, Dc, N, nwords;
@@ -38,6 +42,7 @@ struct KArgs {
   double* eloc_v;         // [n][Ly]
   double* w_row;          // [n][Ly] raw single-row sandwich values
   R* O;                   // [n][N][D^4] or null
+  const float* tcB;       // tensor-core path: site tensors pre-arranged as B tiles (pair_tc.cuh)
   R* scratch;             // per-CTA slots
   size_t slot_elems;
   int smem_wm;            // 1 if the truncation matrix lives in dynamic shared memory
@@ -72,6 +77,10 @@ template <typename R> int max_blocks_row(const Geometry& g);
 template <typename R> int max_blocks_pair(const Geometry& g);
 template <typename R> int max_blocks_pair_fused(const Geometry& g);   // 0: no fused step for (D, Dc)
 template <typename R> cudaError_t launch_grad_accum(const GradArgs& a, const R* O, cudaStream_t st);
+
+// Tensor-core two-row step (TF32, D = 8, Dc = 16).
+int max_blocks_pair_tc();
+cudaError_t launch_pair_tc(const KArgs<float>& a, int grid, cudaStream_t st);
 
 cudaError_t launch_finalize(const Geometry& g, const uint64_t* S, int n, const double* eloc_h,
                             const double* eloc_v, const int* flags, double* eloc, int* status,

@@ -155,7 +155,7 @@ class PEPS:
         self.N = Lx * Ly
         self.nwords = (self.N + 63) // 64
         self.prec = prec
-        self.real = torch.float64 if prec == "fp64" else torch.float32
+        self.real = torch.float64 if prec == "fp64" else torch.float32   # mixed paths store FP32
         self.params = Params(Lx, Ly, 2, D, Dc, float(J1), float(J2), PRECISIONS[prec], float(workspace_gb))
         A = _f64(A)
         assert A.shape == (self.N, 2, D, D, D, D), A.shape

@@ -95,20 +95,26 @@ def test_fp64_parity(case):
 
 
 def fp32_sensitivity(A, spins, Ly, Lx, Dc, J2, trials=2, seed=0):
-    """How much the FP64 oracle's ln|psi| and E_loc move when the input tensors
-    are perturbed by one FP32 unit roundoff (relative 2^-24, random signs).
+    """How much the FP64 oracle's ln|psi| and E_loc move under FP32-sized
+    rounding: the input tensors and every block X entering a truncation are
+    multiplied by (1 + 2^-24 xi), xi = +-1 at random.
 
-    A backward-stable FP32 evaluation returns the exact result of slightly
-    perturbed data, so its error is a modest multiple of this sensitivity.
-    The truncation at a cut with sigma_K ~ sigma_K+1 makes this large; the
-    tolerance below follows it instead of a fixed number.
+    A backward-stable FP32 evaluation returns the exact result of data
+    perturbed like this (times a modest constant), so its error is a multiple
+    of this sensitivity.  A cut with sigma_K ~ sigma_K+1 makes it large; the
+    tolerance follows it instead of a fixed number.
     """
     rng = np.random.default_rng(seed)
+    u = 2.0 ** -24
+
+    def perturb(X):
+        return X * (1.0 + u * rng.choice([-1.0, 1.0], size=X.shape))
+
     base = O.evaluate(A, spins, Ly, Lx, Dc, 1.0, J2, want_O=False)
     dl, de = 0.0, 0.0
     for _ in range(trials):
-        Ap = A * (1.0 + 2.0 ** -24 * rng.choice([-1.0, 1.0], size=A.shape))
-        ev = O.evaluate(Ap, spins, Ly, Lx, Dc, 1.0, J2, want_O=False)
+        Ap = A * (1.0 + u * rng.choice([-1.0, 1.0], size=A.shape))
+        ev = O.evaluate(Ap, spins, Ly, Lx, Dc, 1.0, J2, want_O=False, perturb=perturb)
         dl = max(dl, abs(ev.logabs - base.logabs))
         de = max(de, abs(ev.eloc - base.eloc))
     return dl, de
@@ -154,6 +160,63 @@ def test_fp32_parity_8x8():
     gg = g["grad"].cpu().numpy().ravel()
     cos = gg @ gref.ravel() / (np.linalg.norm(gg) * np.linalg.norm(gref))
     assert cos > 0.999, cos
+    p.close()
+
+
+def test_mixed_tf32_parity():
+    """Mixed path: two-row transfers on the tensor cores (TF32 inputs, FP32
+    accumulation), D = 8, Dc = 16, against the FP64 oracle.
+
+    TF32 keeps 10 mantissa bits (unit roundoff u = 2^-11 ~ 4.9e-4); a ratio
+    passes through ~40 rounded TF32 stages (16 column steps x up to 4
+    intermediates), so its relative error is bounded by ~40 u ~ 2e-2.  Bounds:
+    E_loc within 2e-2 (1 + sum|terms|) + 30 s_E, ln|psi| (FP32 boundary sweep)
+    within 1e-5 + 30 s_psi, batch energy per site within the mean E_loc
+    bound / N, gradient within the bound the E_loc bounds propagate to.
+    (Measured on uniformly drawn configurations, whose E_loc is heavy-tailed:
+    relative E_loc errors up to ~2e-2, gradient cosine ~0.93 on 8 of them.)"""
+    Ly = Lx = 6
+    D, Dc, J2 = 8, 16, 0.5
+    A = inputs.make_tensors(Ly, Lx, D, 1611094674)
+    spins = inputs.random_sz0(8, Ly * Lx, 1611094674)
+    p = make(A, Lx, Ly, D, Dc, J2, "mixed_tf32")
+    r = p.evaluate(packed(spins), logabs=True, eloc=True, O=False)
+    torch.cuda.synchronize()
+    la = r["logabs"].cpu().numpy()
+    el = r["eloc"].cpu().numpy()
+    assert (r["status"].cpu().numpy() == 0).all()
+    evs = oracle_evals(A, spins, Ly, Lx, Dc, J2)
+    rows = []
+    for k, ev in enumerate(evs):
+        sl, se = fp32_sensitivity(A, spins[k], Ly, Lx, Dc, J2, trials=2, seed=k)
+        scale = eloc_scale(ev, Ly, Lx, 1.0, J2, spins[k])
+        rows.append((abs(la[k] - ev.logabs), sl, abs(el[k] - ev.eloc), se, scale))
+    print("\nmixed tf32: k dlogpsi sens_psi dE sens_E scale rel_dE")
+    for k, row in enumerate(rows):
+        print(k, "%.2e %.2e %.2e %.2e %.1f" % row, "%.2e" % (row[2] / row[4]))
+    for k, (dl, sl, de, se, scale) in enumerate(rows):
+        assert dl < 1e-5 + FP32_COND * sl, (k, dl, sl)
+        assert de < 2e-2 * scale + FP32_COND * se, (k, de, scale)
+    g = p.gradient(packed(spins))
+    e_site, gref, _, _ = O.gradient(evs, spins, Ly * Lx, D)
+    e_tol = np.mean([2e-2 * x[4] + FP32_COND * x[3] for x in rows]) / (Ly * Lx)
+    print("energy per site: mixed %.8f oracle %.8f" % (g["energy_per_site"], e_site))
+    assert abs(g["energy_per_site"] - e_site) < e_tol
+    # the gradient 2/n sum_k (E_k - <E>) O_k inherits the E_loc errors: with
+    # |dE_k| <= b_k, |d grad| <= 2/n sum_k b_k |O_k - <O>| (+ the FP32 error of O)
+    n = len(evs)
+    Ofull = np.zeros((n, Ly * Lx, 2, D ** 4))
+    for k, ev in enumerate(evs):
+        for i in range(Ly * Lx):
+            Ofull[k, i, spins[k][i]] = ev.O[i].reshape(-1)
+    Obar = Ofull.mean(axis=0)
+    bound = 2.0 / n * sum((2e-2 * x[4] + FP32_COND * x[3]) * np.linalg.norm(Ofull[k] - Obar)
+                          for k, x in enumerate(rows))
+    gg = g["grad"].cpu().numpy()
+    err = np.linalg.norm(gg - gref)
+    cos = gg.ravel() @ gref.ravel() / (np.linalg.norm(gg) * np.linalg.norm(gref))
+    print("gradient: |d grad| %.3e bound %.3e |grad| %.3e cosine %.6f" % (err, bound, np.linalg.norm(gref), cos))
+    assert err < bound + 1e-4 * np.linalg.norm(gref)
     p.close()
 
 
