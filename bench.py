@@ -38,11 +38,13 @@ FP32_SIMT_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x m
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="16x16_D8_Dc16")
-    ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64", "mixed_tf32"])
+    ap.add_argument("--prec", default="mixed_tf32", choices=["fp32", "fp64", "mixed_tf32"])
+    ap.add_argument("--compare-fp32", action="store_true",
+                    help="also time the plain FP32 path (1 warm-up, 1 step) on the same workload")
     ap.add_argument("--n", type=int, default=0, help="batch override (probes only; the metric uses the default)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -217,6 +219,8 @@ def run_ours(args, rank, world, local_rank):
         f_cfg = flops.pair_flops_batch(L, L, D, Dc, sample, J2) / len(sample)
     elif top == "row_sandwich":
         f_cfg = flops.row_flops_batch(L, L, D, Dc, sample) / len(sample)
+    elif top == "boundary":
+        f_cfg = flops.boundary_flops(L, L, D, Dc)
     else:
         f_cfg = None
     roofline = None
@@ -247,6 +251,20 @@ def run_ours(args, rank, world, local_rank):
         "kernel_share": share, "gpu_launches": launches, "roofline": roofline, "clocks": clocks, "e2e": e2e,
         "energy_per_site": out["energy_per_site"],
     }
+    if args.compare_fp32 and args.prec != "fp32":
+        p.close()
+        q = PEPS(A, L, L, D, Dc, J1=1.0, J2=J2, prec="fp32")
+        q.gradient(S)
+        torch.cuda.synchronize()
+        c0 = torch.cuda.Event(enable_timing=True)
+        c1 = torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        q.gradient(S)
+        c1.record(stream)
+        torch.cuda.synchronize()
+        ms = c0.elapsed_time(c1)
+        res["plain_fp32"] = {"value": n * world / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "steps": 1, "warmup": 1}
+        q.close()
     return res
 
 

@@ -126,6 +126,52 @@ class Work:
         return total
 
 
+def truncation_flops(m, n, K):
+    """Flops of the kept-subspace computation of an m x n block (the kernel's
+    algorithm): Householder bidiagonalisation 4 P Q^2 - 4 Q^3 / 3 (P = max,
+    Q = min), back-transformation of K vectors ~ 4 P Q K, and C' = U_K^T X
+    2 K m n.  Nothing is computed when K == m (no cut)."""
+    if K >= m:
+        return 0
+    P, Q = max(m, n), min(m, n)
+    return 4 * P * Q * Q - 4 * Q ** 3 // 3 + 4 * P * Q * K + 2 * K * m * n
+
+
+def boundary_flops(Lx, Ly, D, Dc):
+    """One configuration's boundary sweeps: top-down over all rows and
+    bottom-up over rows Ly-1..1 (zip-up contractions + truncations, true
+    bond dimensions)."""
+    bd = bond_dims(Lx, Ly, D, Dc)
+    total = 0
+    for dr in range(2):
+        rows = Ly if dr == 0 else Ly - 1
+        b = [1] * (Lx + 1)
+        for j in range(rows):
+            r = j if dr == 0 else Ly - 1 - j
+            o = (1 if r == Ly - 1 else D) if dr == 0 else (1 if r == 0 else D)
+            i_phys = 1 if j == 0 else D
+            k = 1
+            cols = range(Lx) if j % 2 == 0 else range(Lx - 1, -1, -1)
+            for c in cols:
+                l = 1 if c == 0 else D
+                rr = 1 if c == Lx - 1 else D
+                a_, b_ = b[c], b[c + 1]
+                if j % 2 == 0:
+                    total += 2 * (k * l * i_phys * b_ * a_ + k * b_ * rr * o * l * i_phys)
+                    m, n = k * o, b_ * rr
+                    last = c == Lx - 1
+                else:
+                    total += 2 * (a_ * i_phys * rr * k * b_ + a_ * k * l * o * i_phys * rr)
+                    m, n = o * k, a_ * l
+                    last = c == 0
+                if not last:
+                    K = min(Dc, m, n)
+                    total += truncation_flops(m, n, K)
+                    k = K
+            b = list(bd[dr, j])
+    return total
+
+
 def pair_flops_batch(Lx, Ly, D, Dc, spins, J2=0.5):
     w = Work(Lx, Ly, D, Dc)
     return sum(w.pair_flops(s, J2) for s in spins)
