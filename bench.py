@@ -220,7 +220,7 @@ def run_ours(args, rank, world, local_rank):
     elif top == "row_sandwich":
         f_cfg = flops.row_flops_batch(L, L, D, Dc, sample) / len(sample)
     elif top == "boundary":
-        f_cfg = flops.boundary_flops(L, L, D, Dc)
+        f_cfg = float(flops.boundary_flops(L, L, D, Dc))
     else:
         f_cfg = None
     roofline = None
@@ -302,7 +302,7 @@ def main():
     if args.impl == "reference":
         res = run_reference(args, rank)
         if res is not None:
-            print(json.dumps(res), flush=True)
+            print(json.dumps(res, default=float), flush=True)
         return
     if world > 1:
         import torch
@@ -315,7 +315,7 @@ def main():
     res = run_ours(args, rank, world, local_rank)
     if rank == 0:
         res["cpu_baseline"] = cpu
-        print(json.dumps(res), flush=True)
+        print(json.dumps(res, default=float), flush=True)
     if world > 1:
         import torch
         torch.distributed.destroy_process_group()
