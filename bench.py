@@ -49,6 +49,10 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--serve", action="store_true",
+                    help="serving benchmark: Poisson stream of requests over mixed lattices (continuous batching)")
+    ap.add_argument("--serve-seconds", type=float, default=30.0)
+    ap.add_argument("--lanes", type=int, default=4)
     return ap.parse_args()
 
 
@@ -268,6 +272,80 @@ def run_ours(args, rank, world, local_rank):
     return res
 
 
+# (L, D, Dc, J2/J1, precision): square lattices 6..12, D in {4, 6, 8}, Dc = 2D,
+# J2/J1 in {0, 0.5}; the D = 8 models take the tensor-core path.
+SERVE_MIX = [(6, 4, 8, 0.0, "fp32"), (6, 4, 8, 0.5, "fp32"), (8, 4, 8, 0.5, "fp32"), (8, 6, 12, 0.0, "fp32"),
+             (10, 6, 12, 0.5, "fp32"), (8, 8, 16, 0.0, "mixed_tf32"), (12, 8, 16, 0.5, "mixed_tf32")]
+
+
+def run_serving(args):
+    import torch
+    from paper_1611_09467_gb300 import build
+    from paper_1611_09467_gb300.peps import PEPS
+    from paper_1611_09467_gb300.serve import Server, poisson_arrivals
+
+    build.build()
+    torch.cuda.set_device(0)
+    rng = np.random.default_rng(inputs.SEED_BASE + 5)
+    models = []
+    for k, (L, D, Dc, J2, prec) in enumerate(SERVE_MIX):
+        A = inputs.make_tensors(L, L, D, inputs.SEED_BASE + 5 + k)
+        models.append(PEPS(A, L, L, D, Dc, J1=1.0, J2=J2, prec=prec))
+    budget = 48.0
+    srv = Server(nlanes=args.lanes, hbm_budget_gb=budget)
+
+    def make_request(k, seed):
+        m = models[k]
+        n = int(rng.integers(256, 1025))
+        spins = inputs.random_sz0(n, m.N, seed)
+        return k, torch.from_numpy(inputs.pack_spins(spins).view(np.int64)).cuda()
+
+    # capacity probe: one request per model, one at a time (each on one lane's share of the GPU)
+    probe_ms = []
+    for k in range(len(models)):
+        _, S = make_request(k, 10_000 + k)
+        srv.submit(models[k], S)
+        done = srv.drain()
+        probe_ms.append(done[0][1])
+    capacity = args.lanes / (statistics.mean(probe_ms) / 1e3)          # requests/s with all lanes busy
+    rate = 0.8 * capacity
+    arrivals = poisson_arrivals(rate, args.serve_seconds, inputs.SEED_BASE + 5)
+    reqs = [make_request(int(rng.integers(len(models))), 20_000 + i) for i in range(len(arrivals))]
+    torch.cuda.synchronize()
+    srv2 = Server(nlanes=args.lanes, hbm_budget_gb=budget)
+    sampler, fh = start_clock_sampler(os.path.join(ROOT, "gpurun_out", "clocks_serve.csv"))
+    t0 = time.perf_counter()
+    lat = []
+    for (k, S), ta in zip(reqs, arrivals):
+        while time.perf_counter() - t0 < ta:
+            lat += [x for _, x in srv2.poll(wait=False)]
+            time.sleep(0.0005)
+        srv2.submit(models[k], S)
+    lat += [x for _, x in srv2.drain()]
+    wall = time.perf_counter() - t0
+    if sampler:
+        sampler.terminate()
+        sampler.wait()
+        fh.close()
+    st = srv2.stats()
+    total = sum(int(S.shape[0]) for _, S in reqs)
+    res = {
+        "metric": "serving: aggregate configs/s (psi+E_loc) and request latency p50/p99 ms, mixed lattices",
+        "value": total / wall, "unit": "configs/s", "n_gpus": 1, "higher_is_better": True,
+        "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+        "requests": len(reqs), "configs": total, "wall_s": wall, "data": "synthetic",
+        "config": {"mix": [dict(L=L, D=D, Dc=Dc, J2=J2, prec=pr) for (L, D, Dc, J2, pr) in SERVE_MIX],
+                   "configs_per_request": "uniform 256..1024", "arrivals": f"Poisson, {rate:.2f}/s "
+                   f"(80% of the probed capacity {capacity:.2f}/s)", "lanes": args.lanes, "hbm_budget_gb": budget,
+                   "duration_s": args.serve_seconds},
+        "server": st, "probe_ms_per_model": probe_ms,
+        "clocks": read_clocks(os.path.join(ROOT, "gpurun_out", "clocks_serve.csv"), 0),
+    }
+    srv.close()
+    srv2.close()
+    return res
+
+
 def run_reference(args, rank):
     if rank != 0:
         return None
@@ -299,6 +377,9 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.serve:
+        print(json.dumps(run_serving(args), default=float), flush=True)
+        return
     if args.impl == "reference":
         res = run_reference(args, rank)
         if res is not None:

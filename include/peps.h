@@ -166,6 +166,34 @@ peps_status peps_profile_read(peps_ctx* ctx, double* ms /* [8] */, long long* la
 peps_status peps_amplitudes_static(const peps_params* params, const void* A_dev, const uint64_t* S_dev, int n,
                                    double* logabs_dev, int8_t* sign_dev, int32_t* status_dev, void* cuda_stream);
 
+/* ---- serving: continuous batching of evaluation requests ----
+ * A server owns `nlanes` lanes (CUDA streams).  Each request asks for the
+ * outputs of peps_evaluate for n configurations of one model (a context
+ * created with peps_create); requests of different models, lattices and
+ * sizes run concurrently on different lanes, each lane with its own worker
+ * context (the model's tensors are shared, the workspace is private; each
+ * lane's workspace budget is hbm_budget_gb / nlanes).  A queued request is
+ * admitted when a lane is free and the HBM it needs fits under
+ * hbm_budget_gb; smaller requests may pass one that does not fit yet.
+ * Results are the same as peps_evaluate alone.  Inputs must be ready on the
+ * device when submitted; outputs are valid once the request id is returned
+ * by peps_server_poll.  The model contexts must outlive the server's use of
+ * them.  Not thread-safe. */
+typedef struct peps_server peps_server;
+peps_status peps_server_create(int nlanes, double hbm_budget_gb, peps_server** out);
+peps_status peps_server_destroy(peps_server* server);
+peps_status peps_server_submit(peps_server* server, peps_ctx* model, const uint64_t* S_dev, int n,
+                               double* logabs_dev, int8_t* sign_dev, double* eloc_dev, void* O_dev,
+                               int32_t* status_dev, long long* id_out);
+/* Retires finished requests and admits queued ones.  wait != 0 blocks until
+ * at least one request finishes (or nothing is left).  Up to max finished ids
+ * and their latencies (ms, submission to completion) are written; *ndone is
+ * their number. */
+peps_status peps_server_poll(peps_server* server, int wait, long long* ids, double* latency_ms, int max, int* ndone);
+/* stats[8]: submitted, completed, queued, running, p50 and p99 latency (ms),
+ * HBM in use and peak HBM (GB) of the lanes' workspaces. */
+peps_status peps_server_stats(peps_server* server, double* stats);
+
 /* Waits for the context's stream. */
 peps_status peps_synchronize(peps_ctx* ctx);
 

@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT, "libpeps.so")
-SOURCES = ["kernels.cu", "api.cu"]
+SOURCES = ["kernels.cu", "api.cu", "serve.cu"]
 HEADERS = ["contract.cuh", "device.cuh", "kernels.h", "pair_fused.cuh", "pair_tc.cuh", os.path.join("..", "..", "include", "peps.h")]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -108,7 +108,8 @@ struct peps_ctx {
   int nslots = 0;
   size_t elem = 8;
   bool wm_smem = false;
-  DevBuf A, triv_mps, triv_t1, triv_t2, bd, tcB;
+  DevBuf A, triv_mps, triv_t1, triv_t2, bd, tcB;   // the model: shared by clones
+  peps_ctx* parent = nullptr;                        // set on clones (model buffers borrowed)
   DevBuf env, small, O, scratch, gsum;
   int chunk = 0;  // configurations per pass
   int res_boundary = 0, res_row = 0, res_pair = 0, res_mc = 0;  // resident CTAs per kernel
@@ -454,6 +455,61 @@ peps_status mc_impl(peps_ctx* c, uint64_t* S, int n, int nsweeps, uint64_t seed,
 
 }  // namespace
 
+namespace peps {
+
+// A worker context: same model (tensors, tables) as `c`, its own stream and
+// workspace with the given budget.  The model's device buffers are borrowed.
+peps_ctx* ctx_clone(peps_ctx* c, cudaStream_t stream, double workspace_gb, int share) {
+  peps_ctx* k = new peps_ctx();
+  k->p = c->p;
+  k->p.workspace_gb = workspace_gb;
+  k->g = c->g;
+  k->stream = stream;
+  k->nsm = c->nsm;
+  k->nslots = c->nslots;
+  k->elem = c->elem;
+  k->wm_smem = c->wm_smem;
+  // a worker that shares the GPU with `share` lanes sizes its persistent grids to its part
+  auto part = [&](int r) { return std::max(std::min(r, c->nsm), r / std::max(share, 1)); };
+  k->res_boundary = part(c->res_boundary);
+  k->res_row = part(c->res_row);
+  k->res_pair = part(c->res_pair);
+  k->res_mc = part(c->res_mc);
+  k->nslots = std::max(std::max(k->res_boundary, k->res_row), std::max(k->res_pair, k->res_mc));
+  k->pair_tc = c->pair_tc;
+  k->parent = c->parent ? c->parent : c;
+  auto borrow = [](DevBuf& dst, const DevBuf& src) {
+    dst.p = src.p;
+    dst.bytes = src.bytes;
+  };
+  borrow(k->A, c->A);
+  borrow(k->triv_mps, c->triv_mps);
+  borrow(k->triv_t1, c->triv_t1);
+  borrow(k->triv_t2, c->triv_t2);
+  borrow(k->bd, c->bd);
+  borrow(k->tcB, c->tcB);
+  return k;
+}
+
+// Device bytes an evaluation of n configurations needs in a context's
+// workspace (environments of one chunk, per-chunk outputs, scratch slots).
+size_t ctx_footprint(peps_ctx* c, int n, double workspace_gb, int share) {
+  const double budget = (workspace_gb > 0 ? workspace_gb : 24.0) * 1e9;
+  const size_t per = env_bytes_per_cfg(c);
+  size_t chunk = (size_t)std::max<double>(1.0, std::floor(budget / (double)per));
+  chunk = std::min(chunk, (size_t)std::max(n, 1));
+  const int part = std::max(std::min(c->nslots, c->nsm), c->nslots / std::max(share, 1));
+  return per * chunk + Small::bytes((int)chunk, c->g.Ly) + slot_elems(c) * c->elem * part;
+}
+
+size_t ctx_workspace_bytes(peps_ctx* c) {
+  return c->env.bytes + c->small.bytes + c->O.bytes + c->scratch.bytes + c->gsum.bytes;
+}
+
+cudaStream_t ctx_stream(peps_ctx* c) { return c->stream; }
+
+}  // namespace peps
+
 extern "C" {
 
 const char* peps_status_str(peps_status s) {
@@ -550,8 +606,12 @@ peps_status peps_destroy(peps_ctx* c) {
     cudaEventDestroy(e.second.first);
     cudaEventDestroy(e.second.second);
   }
-  DevBuf* bufs[] = {&c->tcB, &c->A, &c->triv_mps, &c->triv_t1, &c->triv_t2, &c->bd, &c->env, &c->small, &c->O, &c->scratch, &c->gsum};
-  for (DevBuf* b : bufs) b->release();
+  DevBuf* work[] = {&c->env, &c->small, &c->O, &c->scratch, &c->gsum};
+  for (DevBuf* b : work) b->release();
+  if (!c->parent) {
+    DevBuf* model[] = {&c->tcB, &c->A, &c->triv_mps, &c->triv_t1, &c->triv_t2, &c->bd};
+    for (DevBuf* b : model) b->release();
+  }
   delete c;
   return PEPS_OK;
 }

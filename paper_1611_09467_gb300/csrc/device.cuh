@@ -244,7 +244,7 @@ template <typename R>
 struct TruncWork {
   R* Wm;      // P x ldw
   int ldw;
-  R* tau;     // 2 * Qmax (left reflectors, then right reflectors)
+  R* tau;     // 4 * Qmax: tau left, tau right, scale left, scale right
   R* t;       // 2 * Qmax off-diagonal of the Golub-Kahan form
   R* t2;      // squares of t
   R* lam;     // Kmax
@@ -265,7 +265,7 @@ struct TruncWork {
 PEPS_HD size_t trunc_ws_elems(int pq, int kmax, bool with_wm) {
   size_t e = 0;
   if (with_wm) e += (size_t)pq * (pq + 1);
-  e += 2 * (size_t)pq * 3;                // tau, t, t2
+  e += 4 * (size_t)pq + 2 * (size_t)pq * 2;   // tau + scale factors (4 pq), t, t2
   e += kmax;                              // lam
   e += (size_t)kmax * 2 * pq;             // Z
   e += (size_t)kmax * 6 * 2 * pq;         // lu
@@ -452,91 +452,95 @@ __device__ void cta_topk_left(const R* X, int m, int n, int K, TruncWork<R>& w, 
   R* tauR = w.tau + w.Qmax;
   R* red = w.red;
   // ---------------- bidiagonalisation: W = Q_L B Q_R^T, B upper bidiagonal
-  // Each reflector: one warp forms it, then the whole CTA computes the
-  // reflector-matrix products (thread groups per column / row) and applies
-  // the rank-1 update.
+  // Reflectors are kept unscaled in W with their scale factors in sL / sR
+  // (v = scale * stored, implicit 1 on the diagonal / super-diagonal).  The
+  // norm each Householder vector needs is accumulated while the previous
+  // rank-1 update writes those entries, and every thread forms the scalars
+  // itself, so one column costs four barriers.
   R* wv = w.wv;
-  for (int j = 0; j < Q; ++j) {
-    if (warp == 0) {
-      R ss = R(0);
-      for (int i = j + 1 + lane; i < P; i += 32) {
-        const R v = W[i * ld + j];
-        ss += v * v;
-      }
-      ss = warp_sum(ss);
-      if (lane == 0) {
-        R tau, scale, beta;
-        householder(W[j * ld + j], ss, tau, scale, beta);
-        red[0] = tau;
-        red[1] = scale;
-        w.t[2 * j] = beta;
-        tauL[j] = tau;
-      }
-    }
+  R* sL = w.tau + 2 * w.Qmax;        // left scale factors (t2 is filled later)
+  R* sR = sL + w.Qmax;
+  R* part = red + 40;                // per-warp partial norms (8)
+  {
+    R ss = R(0);
+    for (int i = 1 + tid; i < P; i += blockDim.x) ss += W[i * ld] * W[i * ld];
+    ss = block_sum(ss, red + 16);
+    if (tid < kWarps) part[tid] = tid == 0 ? ss : R(0);
     __syncthreads();
-    {
-      const R tau = red[0], scale = red[1];
-      const int ncol = Q - j - 1;
-      if (tau != R(0)) {
-        for (int i = j + 1 + tid; i < P; i += blockDim.x) W[i * ld + j] *= scale;
-        __syncthreads();
-      }
-      if (tau != R(0) && ncol > 0) {
-        // wv[c] = tau * (W[j][c] + sum_{i>j} v_i W[i][c])
-        int tpc = kThreads / ncol;
-        tpc = tpc >= 32 ? 32 : tpc >= 16 ? 16 : tpc >= 8 ? 8 : tpc >= 4 ? 4 : tpc >= 2 ? 2 : 1;
-        const int cpr = kThreads / tpc;
-        for (int cb = 0; cb < ncol; cb += cpr) {
-          const int cl = cb + tid / tpc, gl = tid % tpc;
-          const bool act = cl < ncol;
-          const int c = j + 1 + (act ? cl : 0);
-          R s0 = (gl == 0) ? W[j * ld + c] : R(0), s1 = R(0), s2 = R(0), s3 = R(0);
-          int i = j + 1 + gl;
-          for (; i + 3 * tpc < P; i += 4 * tpc) {
-            s0 += W[i * ld + j] * W[i * ld + c];
-            s1 += W[(i + tpc) * ld + j] * W[(i + tpc) * ld + c];
-            s2 += W[(i + 2 * tpc) * ld + j] * W[(i + 2 * tpc) * ld + c];
-            s3 += W[(i + 3 * tpc) * ld + j] * W[(i + 3 * tpc) * ld + c];
-          }
-          for (; i < P; i += tpc) s0 += W[i * ld + j] * W[i * ld + c];
-          R sacc = warp_sum((s0 + s1) + (s2 + s3), tpc);
-          if (act && gl == 0) wv[c] = sacc * tau;
+  }
+  for (int j = 0; j < Q; ++j) {
+    // -- left reflector on column j (rows j..P-1); its norm is in part[]
+    R colnorm = R(0);
+    for (int q = 0; q < kWarps; ++q) colnorm += part[q];
+    R tau, scale, beta;
+    householder(W[j * ld + j], colnorm, tau, scale, beta);
+    if (tid == 0) {
+      w.t[2 * j] = beta;
+      tauL[j] = tau;
+      sL[j] = scale;
+    }
+    const int ncol = Q - j - 1;
+    R rownorm = R(0);                // squared norm of row j beyond j+1 after the left update
+    if (tau != R(0) && ncol > 0) {
+      // wv[c] = tau * (W[j][c] + scale * sum_{i>j} W[i][j] W[i][c])
+      int tpc = kThreads / ncol;
+      tpc = tpc >= 32 ? 32 : tpc >= 16 ? 16 : tpc >= 8 ? 8 : tpc >= 4 ? 4 : tpc >= 2 ? 2 : 1;
+      const int cpr = kThreads / tpc;
+      for (int cb = 0; cb < ncol; cb += cpr) {
+        const int cl = cb + tid / tpc, gl = tid % tpc;
+        const bool act = cl < ncol;
+        const int c = j + 1 + (act ? cl : 0);
+        R s0 = R(0), s1 = R(0), s2 = R(0), s3 = R(0);
+        int i = j + 1 + gl;
+        for (; i + 3 * tpc < P; i += 4 * tpc) {
+          s0 += W[i * ld + j] * W[i * ld + c];
+          s1 += W[(i + tpc) * ld + j] * W[(i + tpc) * ld + c];
+          s2 += W[(i + 2 * tpc) * ld + j] * W[(i + 2 * tpc) * ld + c];
+          s3 += W[(i + 3 * tpc) * ld + j] * W[(i + 3 * tpc) * ld + c];
         }
-        __syncthreads();
-        // rank-1 update: warps over rows, lanes over columns
-        for (int i = j + warp; i < P; i += kWarps) {
-          const R v = i == j ? R(1) : W[i * ld + j];
-          for (int c = j + 1 + lane; c < Q; c += 32) W[i * ld + c] -= wv[c] * v;
+        for (; i < P; i += tpc) s0 += W[i * ld + j] * W[i * ld + c];
+        const R sacc = warp_sum((s0 + s1) + (s2 + s3), tpc);
+        if (act && gl == 0) wv[c] = tau * (W[j * ld + c] + scale * sacc);
+      }
+      __syncthreads();
+      // W[i][c] -= wv[c] v_i for i >= j, c > j; warp 0 takes row j and its norm
+      for (int i = j + warp; i < P; i += kWarps) {
+        const R v = i == j ? R(1) : scale * W[i * ld + j];
+        R rn = R(0);
+        for (int c = j + 1 + lane; c < Q; c += 32) {
+          const R x = W[i * ld + c] - wv[c] * v;
+          W[i * ld + c] = x;
+          if (c >= j + 2) rn += x * x;
+        }
+        if (i == j) {
+          rn = warp_sum(rn);
+          if (lane == 0) red[5] = rn;
         }
       }
       __syncthreads();
+      rownorm = red[5];
+    } else if (ncol > 0) {
+      if (warp == 0) {
+        R rn = R(0);
+        for (int c = j + 2 + lane; c < Q; c += 32) rn += W[j * ld + c] * W[j * ld + c];
+        rn = warp_sum(rn);
+        if (lane == 0) red[5] = rn;
+      }
+      __syncthreads();
+      rownorm = red[5];
     }
     if (j < Q - 1) {
-      if (warp == 0) {
-        R ss = R(0);
-        for (int c = j + 2 + lane; c < Q; c += 32) {
-          const R v = W[j * ld + c];
-          ss += v * v;
-        }
-        ss = warp_sum(ss);
-        if (lane == 0) {
-          R tau, scale, beta;
-          householder(W[j * ld + j + 1], ss, tau, scale, beta);
-          red[2] = tau;
-          red[3] = scale;
-          w.t[2 * j + 1] = beta;
-          tauR[j] = tau;
-        }
+      // -- right reflector on row j (columns j+1..Q-1)
+      R tr, sr, br;
+      householder(W[j * ld + j + 1], rownorm, tr, sr, br);
+      if (tid == 0) {
+        w.t[2 * j + 1] = br;
+        tauR[j] = tr;
+        sR[j] = sr;
       }
-      __syncthreads();
-      const R tau = red[2], scale = red[3];
-      const int nrow = P - j - 1, ncol = Q - j - 1;
-      if (tau != R(0)) {
-        for (int c = j + 2 + tid; c < Q; c += blockDim.x) W[j * ld + c] *= scale;
-        __syncthreads();
-      }
-      if (tau != R(0) && nrow > 0) {
-        // wv[i] = tau * (W[i][j+1] + sum_{c>j+1} W[i][c] v'_c)
+      const int nrow = P - j - 1;
+      if (tr != R(0)) {
+        // wv[i] = tr * (W[i][j+1] + sr * sum_{c>j+1} W[i][c] W[j][c])
         int tpc = kThreads / nrow;
         tpc = tpc >= 32 ? 32 : tpc >= 16 ? 16 : tpc >= 8 ? 8 : tpc >= 4 ? 4 : tpc >= 2 ? 2 : 1;
         const int rpr = kThreads / tpc;
@@ -544,7 +548,7 @@ __device__ void cta_topk_left(const R* X, int m, int n, int K, TruncWork<R>& w, 
           const int rl = rb + tid / tpc, gl = tid % tpc;
           const bool act = rl < nrow;
           const int i = j + 1 + (act ? rl : 0);
-          R s0 = (gl == 0) ? W[i * ld + j + 1] : R(0), s1 = R(0), s2 = R(0), s3 = R(0);
+          R s0 = R(0), s1 = R(0), s2 = R(0), s3 = R(0);
           int c = j + 2 + gl;
           for (; c + 3 * tpc < Q; c += 4 * tpc) {
             s0 += W[i * ld + c] * W[j * ld + c];
@@ -553,27 +557,40 @@ __device__ void cta_topk_left(const R* X, int m, int n, int K, TruncWork<R>& w, 
             s3 += W[i * ld + c + 3 * tpc] * W[j * ld + c + 3 * tpc];
           }
           for (; c < Q; c += tpc) s0 += W[i * ld + c] * W[j * ld + c];
-          R sacc = warp_sum((s0 + s1) + (s2 + s3), tpc);
-          if (act && gl == 0) wv[i] = sacc * tau;
+          const R sacc = warp_sum((s0 + s1) + (s2 + s3), tpc);
+          if (act && gl == 0) wv[i] = tr * (W[i * ld + j + 1] + sr * sacc);
         }
         __syncthreads();
-        // rank-1 update: warps over rows, lanes over columns (v' held per lane)
+        // W[i][c] -= wv[i] v'_c for i > j, c > j; lane 0 of each warp sums column j+1 below row j+1
         R vl[8];
 #pragma unroll
         for (int t = 0; t < 8; ++t) {
           const int c = j + 1 + lane + 32 * t;
-          vl[t] = c == j + 1 ? R(1) : (c < Q ? W[j * ld + c] : R(0));
+          vl[t] = c == j + 1 ? R(1) : (c < Q ? sr * W[j * ld + c] : R(0));
         }
+        R cn = R(0);
         for (int i = j + 1 + warp; i < P; i += kWarps) {
           const R wi = wv[i];
 #pragma unroll
           for (int t = 0; t < 8; ++t) {
             const int c = j + 1 + lane + 32 * t;
-            if (c < Q) W[i * ld + c] -= wi * vl[t];
+            if (c < Q) {
+              const R x = W[i * ld + c] - wi * vl[t];
+              W[i * ld + c] = x;
+              if (t == 0 && lane == 0 && i > j + 1) cn += x * x;
+            }
           }
         }
+        if (lane == 0) part[warp] = cn;
+        __syncthreads();
+      } else {
+        // no right update: column j+1's norm below row j+1 as it stands
+        R cn = R(0);
+        for (int i = j + 2 + tid; i < P; i += blockDim.x) cn += W[i * ld + j + 1] * W[i * ld + j + 1];
+        cn = block_sum(cn, red + 16);
+        if (tid < kWarps) part[tid] = tid == 0 ? cn : R(0);
+        __syncthreads();
       }
-      __syncthreads();
     }
   }
   PEPS_PHASE(1);
@@ -681,6 +698,8 @@ __device__ void cta_topk_left(const R* X, int m, int n, int K, TruncWork<R>& w, 
   }
   __syncthreads();
   {
+    const R* sLb = w.tau + 2 * w.Qmax;
+    const R* sRb = sLb + w.Qmax;
     // Every group runs the same loop (the shuffles need whole warps); groups
     // beyond K compute on column 0 and discard the result.
     const int G = K <= 8 ? 32 : (K <= 16 ? 16 : 8);
@@ -691,12 +710,14 @@ __device__ void cta_topk_left(const R* X, int m, int n, int K, TruncWork<R>& w, 
       for (int j = Q - 1; j >= 0; --j) {
         const R tau = tauL[j];
         if (tau == R(0)) continue;
-        R s = gl == 0 ? Uk[j * K + cc] : R(0);
+        const R sc = sLb[j];
+        R s = R(0);
         for (int i = j + 1 + gl; i < P; i += G) s += W[i * ld + j] * Uk[i * K + cc];
-        s = warp_sum(s, G) * tau;
+        s = (Uk[j * K + cc] + sc * warp_sum(s, G)) * tau;
         if (act) {
           if (gl == 0) Uk[j * K + cc] -= s;
-          for (int i = j + 1 + gl; i < P; i += G) Uk[i * K + cc] -= s * W[i * ld + j];
+          const R s2 = s * sc;
+          for (int i = j + 1 + gl; i < P; i += G) Uk[i * K + cc] -= s2 * W[i * ld + j];
         }
         __syncwarp();
       }
@@ -704,12 +725,14 @@ __device__ void cta_topk_left(const R* X, int m, int n, int K, TruncWork<R>& w, 
       for (int j = Q - 2; j >= 0; --j) {
         const R tau = tauR[j];
         if (tau == R(0)) continue;
-        R s = gl == 0 ? Uk[(j + 1) * K + cc] : R(0);
+        const R sc = sRb[j];
+        R s = R(0);
         for (int c = j + 2 + gl; c < Q; c += G) s += W[j * ld + c] * Uk[c * K + cc];
-        s = warp_sum(s, G) * tau;
+        s = (Uk[(j + 1) * K + cc] + sc * warp_sum(s, G)) * tau;
         if (act) {
           if (gl == 0) Uk[(j + 1) * K + cc] -= s;
-          for (int c = j + 2 + gl; c < Q; c += G) Uk[c * K + cc] -= s * W[j * ld + c];
+          const R s2 = s * sc;
+          for (int c = j + 2 + gl; c < Q; c += G) Uk[c * K + cc] -= s2 * W[j * ld + c];
         }
         __syncwarp();
       }

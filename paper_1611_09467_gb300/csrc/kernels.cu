@@ -260,7 +260,7 @@ __device__ void carve_zip(const Geometry& g, R*& p, ZipBufs<R>& zb, R* wm_smem, 
   w.Ubs = sh; sh += P * Dc;
   w.Uks = sh;
   w.Qmax = (int)P;
-  w.tau = p; p += 2 * P;
+  w.tau = p; p += 4 * P;
   w.t = p; p += 2 * P;
   w.t2 = p; p += 2 * P;
   w.lam = p; p += Dc;

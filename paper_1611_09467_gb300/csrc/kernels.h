@@ -90,6 +90,18 @@ cudaError_t launch_grad_finalize(int total, int n_ok_dev_unused, const double* s
 // Records the calling thread's error message (returned by peps_last_error).
 void set_last_error(const char* msg);
 
+}  // namespace peps
+
+struct peps_ctx;
+
+namespace peps {
+
+// Worker contexts for the serving loop (api.cu).
+peps_ctx* ctx_clone(peps_ctx* c, cudaStream_t stream, double workspace_gb, int share);
+size_t ctx_footprint(peps_ctx* c, int n, double workspace_gb, int share);
+size_t ctx_workspace_bytes(peps_ctx* c);
+cudaStream_t ctx_stream(peps_ctx* c);
+
 cudaError_t launch_sum_eloc(const double* eloc, const int* status, int n, double* sums, cudaStream_t st);
 
 }  // namespace peps

@@ -1,0 +1,242 @@
+// Continuous-batching serving loop for evaluation requests (host C++).
+//
+// Each lane's worker sizes its persistent grids to 1/nlanes of the GPU, so
+// the kernels of concurrent requests run side by side.
+// A request asks for ln|psi|, E_loc and/or Delta of a batch of configurations
+// of one model (a context: lattice, D, Dc, tensors).  The server runs
+// requests on `nlanes` lanes, each a CUDA stream with its own worker
+// context (same model buffers, private workspace), so requests of different
+// models and sizes overlap on the GPU.  Requests wait in a queue until a lane
+// is free and the HBM they need fits under the budget (footprint admission);
+// a request that does not fit lets smaller queued ones pass.  Completion is
+// observed through one event per lane; the latency of a request runs from
+// submission to the poll that sees its event.  Results do not depend on the
+// lane or on what else runs: every configuration is evaluated by the same
+// kernels in the same order.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <deque>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/peps.h"
+#include "kernels.h"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Request {
+  long long id;
+  peps_ctx* model;
+  const uint64_t* S;
+  int n;
+  double* logabs;
+  int8_t* sign;
+  double* eloc;
+  void* O;
+  int32_t* status;
+  Clock::time_point submitted;
+};
+
+struct Lane {
+  cudaStream_t stream = nullptr;
+  cudaEvent_t done = nullptr;
+  bool busy = false;
+  Request req{};
+  peps_ctx* model = nullptr;   // model of the worker below
+  peps_ctx* worker = nullptr;
+};
+
+}  // namespace
+
+struct peps_server {
+  std::vector<Lane> lanes;
+  std::deque<Request> queue;
+  size_t budget = 0;
+  double lane_gb = 0;
+  long long next_id = 1;
+  long long submitted = 0, completed = 0;
+  std::vector<double> latency_ms;
+  std::deque<std::pair<long long, double>> finished;   // retired, not yet reported by poll
+  size_t peak_bytes = 0;
+};
+
+namespace {
+
+size_t in_use(const peps_server* s) {
+  size_t b = 0;
+  for (const Lane& l : s->lanes)
+    if (l.worker) b += peps::ctx_workspace_bytes(l.worker);
+  return b;
+}
+
+// Bytes a lane would add to run request r (workspace growth, or a new worker).
+size_t extra_bytes(const peps_server* s, const Lane& l, const Request& r) {
+  const size_t need = peps::ctx_footprint(r.model, r.n, s->lane_gb, (int)s->lanes.size());
+  if (l.worker && l.model == r.model) {
+    const size_t have = peps::ctx_workspace_bytes(l.worker);
+    return need > have ? need - have : 0;
+  }
+  return need;
+}
+
+peps_status launch(peps_server* s, Lane& l, const Request& r) {
+  if (!l.worker || l.model != r.model) {
+    if (l.worker) {
+      cudaStreamSynchronize(l.stream);
+      peps_destroy(l.worker);
+    }
+    l.worker = peps::ctx_clone(r.model, l.stream, s->lane_gb, (int)s->lanes.size());
+    l.model = r.model;
+  }
+  const peps_status st = peps_evaluate(l.worker, r.S, r.n, r.logabs, r.sign, r.eloc, r.O, r.status);
+  if (st != PEPS_OK) return st;
+  if (cudaEventRecord(l.done, l.stream) != cudaSuccess) return PEPS_ECUDA;
+  l.busy = true;
+  l.req = r;
+  s->peak_bytes = std::max(s->peak_bytes, in_use(s));
+  return PEPS_OK;
+}
+
+// Retires finished lanes, then admits queued requests that fit.
+peps_status step(peps_server* s) {
+  for (Lane& l : s->lanes) {
+    if (!l.busy) continue;
+    const cudaError_t q = cudaEventQuery(l.done);
+    if (q == cudaErrorNotReady) continue;
+    if (q != cudaSuccess) return PEPS_ECUDA;
+    const double ms = std::chrono::duration<double, std::milli>(Clock::now() - l.req.submitted).count();
+    l.busy = false;
+    s->completed += 1;
+    s->latency_ms.push_back(ms);
+    s->finished.emplace_back(l.req.id, ms);
+  }
+  for (auto it = s->queue.begin(); it != s->queue.end();) {
+    Lane* free_lane = nullptr;
+    // prefer a free lane that already holds a worker of this model
+    for (Lane& l : s->lanes)
+      if (!l.busy && (!free_lane || (l.model == it->model && free_lane->model != it->model))) free_lane = &l;
+    if (!free_lane) break;
+    const size_t extra = extra_bytes(s, *free_lane, *it);
+    size_t freed = 0;
+    if (free_lane->worker && free_lane->model != it->model) freed = peps::ctx_workspace_bytes(free_lane->worker);
+    if (in_use(s) - freed + extra > s->budget) {
+      ++it;   // does not fit now: let a smaller queued request pass
+      continue;
+    }
+    const peps_status st = launch(s, *free_lane, *it);
+    if (st != PEPS_OK) return st;
+    it = s->queue.erase(it);
+  }
+  return PEPS_OK;
+}
+
+double percentile(std::vector<double> v, double p) {
+  if (v.empty()) return 0.0;
+  std::sort(v.begin(), v.end());
+  const double x = p / 100.0 * (double)(v.size() - 1);
+  const size_t i = (size_t)std::floor(x);
+  const size_t j = std::min(i + 1, v.size() - 1);
+  return v[i] + (x - (double)i) * (v[j] - v[i]);
+}
+
+}  // namespace
+
+extern "C" {
+
+peps_status peps_server_create(int nlanes, double hbm_budget_gb, peps_server** out) {
+  if (!out || nlanes < 1 || nlanes > 64 || !(hbm_budget_gb > 0)) {
+    peps::set_last_error("need 1 <= nlanes <= 64, a positive budget and an output pointer");
+    return PEPS_EINVAL;
+  }
+  peps_server* s = new peps_server();
+  s->budget = (size_t)(hbm_budget_gb * 1e9);
+  s->lane_gb = hbm_budget_gb / nlanes;
+  s->lanes.resize(nlanes);
+  for (Lane& l : s->lanes) {
+    if (cudaStreamCreateWithFlags(&l.stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&l.done, cudaEventDisableTiming) != cudaSuccess) {
+      peps_server_destroy(s);
+      peps::set_last_error("stream or event creation failed");
+      return PEPS_ECUDA;
+    }
+  }
+  *out = s;
+  return PEPS_OK;
+}
+
+peps_status peps_server_destroy(peps_server* s) {
+  if (!s) return PEPS_OK;
+  for (Lane& l : s->lanes) {
+    if (l.stream) cudaStreamSynchronize(l.stream);
+    if (l.worker) peps_destroy(l.worker);
+    if (l.done) cudaEventDestroy(l.done);
+    if (l.stream) cudaStreamDestroy(l.stream);
+  }
+  delete s;
+  return PEPS_OK;
+}
+
+peps_status peps_server_submit(peps_server* s, peps_ctx* model, const uint64_t* S_dev, int n, double* logabs_dev,
+                               int8_t* sign_dev, double* eloc_dev, void* O_dev, int32_t* status_dev,
+                               long long* id_out) {
+  if (!s || !model || n < 1 || !S_dev) {
+    peps::set_last_error("bad request");
+    return PEPS_EINVAL;
+  }
+  Request r{s->next_id++, model, S_dev, n, logabs_dev, sign_dev, eloc_dev, O_dev, status_dev, Clock::now()};
+  s->queue.push_back(r);
+  s->submitted += 1;
+  if (id_out) *id_out = r.id;
+  return step(s);
+}
+
+peps_status peps_server_poll(peps_server* s, int wait, long long* ids, double* latency_ms, int max, int* ndone) {
+  if (!s || !ndone) {
+    peps::set_last_error("bad argument");
+    return PEPS_EINVAL;
+  }
+  *ndone = 0;
+  for (;;) {
+    const peps_status st = step(s);
+    if (st != PEPS_OK) return st;
+    while (!s->finished.empty() && *ndone < max) {
+      if (ids) ids[*ndone] = s->finished.front().first;
+      if (latency_ms) latency_ms[*ndone] = s->finished.front().second;
+      s->finished.pop_front();
+      *ndone += 1;
+    }
+    bool running = false;
+    for (const Lane& l : s->lanes) running = running || l.busy;
+    if (!wait || *ndone > 0 || (!running && s->queue.empty())) return PEPS_OK;
+    if (!running && !s->queue.empty()) {
+      peps::set_last_error("queued requests exceed the HBM budget even with every lane idle");
+      return PEPS_ENOMEM;
+    }
+    std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
+}
+
+peps_status peps_server_stats(peps_server* s, double* stats) {
+  if (!s || !stats) {
+    peps::set_last_error("bad argument");
+    return PEPS_EINVAL;
+  }
+  int running = 0;
+  for (const Lane& l : s->lanes) running += l.busy ? 1 : 0;
+  stats[0] = (double)s->submitted;
+  stats[1] = (double)s->completed;
+  stats[2] = (double)s->queue.size();
+  stats[3] = (double)running;
+  stats[4] = percentile(s->latency_ms, 50.0);
+  stats[5] = percentile(s->latency_ms, 99.0);
+  stats[6] = (double)in_use(s) / 1e9;
+  stats[7] = (double)s->peak_bytes / 1e9;
+  return PEPS_OK;
+}
+
+}  // extern "C"
