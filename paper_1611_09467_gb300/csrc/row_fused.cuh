@@ -1,0 +1,211 @@
+// Fused single-row transfer step and site environment (sandwich
+// <U_{r-1}| row r |L_{r+1}>, Fig. 1c) with every intermediate in shared
+// memory.
+//
+// Direction-normalised form as in pair_fused.cuh.  A single-row transfer is
+// stored [x'][x][y] (x' the bond of L, x the bond of U, y the horizontal
+// bond), so <F_c, G_{c+1}> is an elementwise dot:
+//   left  (F_{c-1} -> F_c): in = (a, a', l), out = (b, b', r)
+//   right (G_{c+1} -> G_c): in = (b, b', r), out = (a, a', l)
+// One step, sliced over the in-bond s of L:
+//   s1: P[(yi,u)][xo]       = sum_xi    Fin[s][xi][yi] Mu[xi][u][xo]
+//   s2: Q[d][(xo,yo)]       = sum_yi,u  P T[yi][yo][u][d]
+//   s3: acc[x'o][(xo,yo)]  += sum_d     Q Md[s][d][x'o]
+// The site environment (the B of Delta = B / W, Sec. II)
+//   B[l,r,u,d] = sum F[a,l,a'] Mu[a,u,b] Md[a',d,b'] G[b,r,b']
+// pairs F with Mu and Md with G first, sliced over a':
+//   X[b][(l,u)]     = sum_a   F[s][a][l] Mu[a][u][b]
+//   Y[b][(d,r)]     = sum_b'  Md[s][d][b'] G[b'][b][r]
+//   acc[(l,u)][(d,r)] += sum_b X Y
+// which needs half the multiply-adds of contracting the three boundary
+// tensors into one block first.  Both are the contractions of
+// col1_left_step / col1_right_step / site_env_step, reordered; results agree
+// to rounding.
+#pragma once
+
+#include "pair_fused.cuh"
+
+namespace peps {
+
+template <int D, int Dc>
+struct RowSmem {
+  static constexpr int DD = D * D, D3 = DD * D, D4 = DD * DD;
+  static constexpr int MU = Dc * D * Dc;   // Mu (step: [xi][(u,xo)]; site env: as stored)
+  static constexpr int T = DD * DD;        // T as [(yi,u)][(yo,d)]
+  static constexpr int FS = Dc * D;        // one slice of a transfer
+  static constexpr int MD = D * Dc;        // one slice of Md
+  static constexpr int P = DD * Dc;        // P[(yi,u)][xo]
+  static constexpr int Q = D * Dc * D;     // Q[d][(xo,yo)]
+  static constexpr int step_total = MU + T + 2 * (FS + MD) + P + Q;   // F and Md slices double-buffered
+  static constexpr int env_total = MU + Dc * FS + MD + FS + 2 * Dc * DD;
+  static constexpr int total = step_total > env_total ? step_total : env_total;
+  static constexpr int OUT = Dc * D * Dc;  // outputs of a step
+  static constexpr int OPT = (OUT + kThreads - 1) / kThreads;   // outputs per thread
+  static constexpr int TM = (DD + 3) / 4;  // 4x4 tiles of the site-env accumulator per dimension
+  static constexpr int TPT = (TM * TM + kThreads - 1) / kThreads;
+  static_assert(D4 <= env_total, "site environment staging must fit the site-env buffers");
+};
+
+// One fused single-row transfer step.  right == false: F_{c-1} -> F_c;
+// right == true: G_{c+1} -> G_c.  Mu, Md: padded [Dc][D][Dc] boundary-MPS
+// tensors of column c; T: padded [l][r][u][d] site tensor at the chosen spin.
+// If Gdot is null the result is written to Fout; otherwise <result, Gdot> is
+// returned (all threads) and nothing is written.  Ends with a barrier.
+template <typename R, int D, int Dc>
+__device__ R row_step_fused(bool right, const R* __restrict__ Fin, R* __restrict__ Fout, const R* __restrict__ Mu,
+                            const R* __restrict__ T, const R* __restrict__ Md, const R* __restrict__ Gdot, R* sm,
+                            R* red) {
+  using S = RowSmem<D, Dc>;
+  constexpr int DD = S::DD, D3 = S::D3, XY = Dc * D;
+  R* Mus = sm;
+  R* Ts = Mus + S::MU;
+  R* Fs0 = Ts + S::T;
+  R* Mds0 = Fs0 + 2 * S::FS;
+  R* Pb = Mds0 + 2 * S::MD;
+  R* Qb = Pb + S::P;
+  const int tid = threadIdx.x;
+  __syncthreads();
+  for (int e = tid; e < S::T; e += kThreads) {
+    const int yin = e / D3, u = (e / DD) % D, yout = (e / D) % D, d = e % D;
+    const int l = right ? yout : yin, r = right ? yin : yout;
+    Ts[e] = T[l * D3 + r * DD + u * D + d];
+  }
+  for (int e = tid; e < S::MU; e += kThreads) {
+    const int xin = e / (D * Dc), u = (e / Dc) % D, xout = e % Dc;
+    const int a = right ? xout : xin, b = right ? xin : xout;
+    Mus[e] = Mu[a * D * Dc + u * Dc + b];
+  }
+  // thread t owns outputs o = q * kThreads + t, o = x'o * XY + (xo, yo)
+  R acc[S::OPT];
+#pragma unroll
+  for (int q = 0; q < S::OPT; ++q) acc[q] = R(0);
+  // three barriers per slice: the slice buffers alternate, so loading slice
+  // s+1 cannot overwrite what s3 of slice s still reads
+  for (int s = 0; s < Dc; ++s) {
+    R* Fs = Fs0 + (s & 1) * S::FS;
+    R* Mds = Mds0 + (s & 1) * S::MD;
+    for (int e = tid; e < S::FS; e += kThreads) Fs[e] = Fin[s * XY + e];   // [xi][yi]
+    for (int e = tid; e < S::MD; e += kThreads) {
+      const int d = e / Dc, xo = e % Dc;
+      Mds[e] = right ? Md[xo * D * Dc + d * Dc + s] : Md[s * D * Dc + d * Dc + xo];
+    }
+    __syncthreads();
+    smem_gemm_km<R, D, D * Dc, Dc>(Fs, Mus, [&](int i, int j, R v) {
+      const int u = j / Dc, xo = j % Dc;      // i = yi, j = (u, xo)
+      Pb[(i * D + u) * Dc + xo] = v;
+    });
+    __syncthreads();
+    smem_gemm_km<R, Dc, DD, DD>(Pb, Ts, [&](int i, int j, R v) {
+      const int yo = j / D, d = j % D;        // i = xo, j = (yo, d)
+      Qb[d * XY + i * D + yo] = v;
+    });
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < S::OPT; ++q) {
+      const int o = q * kThreads + tid;
+      if (S::OUT % kThreads == 0 || o < S::OUT) {
+        const int row = o % XY, xo2 = o / XY;
+        R v = acc[q];
+#pragma unroll
+        for (int d = 0; d < D; ++d) v = fma(Qb[d * XY + row], Mds[d * Dc + xo2], v);
+        acc[q] = v;
+      }
+    }
+  }
+  R dot = R(0);
+#pragma unroll
+  for (int q = 0; q < S::OPT; ++q) {
+    const int o = q * kThreads + tid;
+    if (S::OUT % kThreads == 0 || o < S::OUT) {
+      if (Gdot == nullptr) Fout[o] = acc[q];
+      else dot = fma(acc[q], Gdot[o], dot);
+    }
+  }
+  if (Gdot != nullptr) dot = block_sum(dot, red);
+  else __syncthreads();
+  return dot;
+}
+
+// Site environment of column c, scaled: Bout[l][r][u][d] = scale * B, from
+// F_{c-1} ([a'][a][l]), Mu, Md (padded [Dc][D][Dc]) and G_{c+1} ([b'][b][r]).
+// Ends with a barrier.
+template <typename R, int D, int Dc>
+__device__ void site_env_fused(const R* __restrict__ F, const R* __restrict__ Mu, const R* __restrict__ Md,
+                               const R* __restrict__ G, R scale, R* __restrict__ Bout, R* sm) {
+  using S = RowSmem<D, Dc>;
+  constexpr int DD = S::DD, D3 = S::D3, XY = Dc * D, TM = S::TM;
+  R* Mus = sm;                 // Mu as stored: [a][(u,b)]
+  R* Gs = Mus + S::MU;         // G: [b'][(b,r)]
+  R* Mdk = Gs + Dc * XY;       // slice s of Md: [b'][d]
+  R* Fs = Mdk + S::MD;         // slice s of F: [a][l]
+  R* Xs = Fs + S::FS;          // [b][(l,u)]
+  R* Ys = Xs + Dc * DD;        // [b][(d,r)]
+  const int tid = threadIdx.x;
+  __syncthreads();
+  for (int e = tid; e < S::MU; e += kThreads) Mus[e] = Mu[e];
+  for (int e = tid; e < Dc * XY; e += kThreads) Gs[e] = G[e];
+  R acc[S::TPT][4][4];
+#pragma unroll
+  for (int t = 0; t < S::TPT; ++t)
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[t][i][j] = R(0);
+  for (int s = 0; s < Dc; ++s) {
+    for (int e = tid; e < S::MD; e += kThreads) {
+      const int bp = e / D, d = e % D;
+      Mdk[e] = Md[s * D * Dc + d * Dc + bp];
+    }
+    for (int e = tid; e < S::FS; e += kThreads) Fs[e] = F[s * XY + e];
+    __syncthreads();
+    // X: rows l, cols (u, b), k = a;  Y: rows d, cols (b, r), k = b'
+    smem_gemm_km<R, D, D * Dc, Dc>(Fs, Mus, [&](int i, int j, R v) { Xs[(j % Dc) * DD + i * D + j / Dc] = v; });
+    smem_gemm_km<R, D, Dc * D, Dc>(Mdk, Gs, [&](int i, int j, R v) { Ys[(j / D) * DD + i * D + j % D] = v; });
+    __syncthreads();
+#pragma unroll
+    for (int t = 0; t < S::TPT; ++t) {
+      const int tile = t * kThreads + tid;
+      if ((TM * TM) % kThreads == 0 || tile < TM * TM) {
+        const int i0 = (tile / TM) * 4, j0 = (tile % TM) * 4;
+#pragma unroll 4
+        for (int b = 0; b < Dc; ++b) {
+          R xv[4], yv[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            xv[q] = (DD % 4 == 0 || i0 + q < DD) ? Xs[b * DD + i0 + q] : R(0);
+            yv[q] = (DD % 4 == 0 || j0 + q < DD) ? Ys[b * DD + j0 + q] : R(0);
+          }
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[t][i][j] = fma(xv[i], yv[j], acc[t][i][j]);
+        }
+      }
+    }
+    __syncthreads();
+  }
+  // stage [l][r][u][d] in shared memory, then write coalesced
+  R* Bs = sm;
+#pragma unroll
+  for (int t = 0; t < S::TPT; ++t) {
+    const int tile = t * kThreads + tid;
+    if ((TM * TM) % kThreads == 0 || tile < TM * TM) {
+      const int i0 = (tile / TM) * 4, j0 = (tile % TM) * 4;
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int lu = i0 + i, dr = j0 + j;
+          if ((DD % 4 == 0 || (lu < DD && dr < DD))) {
+            const int l = lu / D, u = lu % D, d = dr / D, r = dr % D;
+            Bs[l * D3 + r * DD + u * D + d] = acc[t][i][j] * scale;
+          }
+        }
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < S::D4; e += kThreads) Bout[e] = Bs[e];
+  __syncthreads();
+}
+
+}  // namespace peps

@@ -82,10 +82,12 @@ class Work:
         return 2 * (l * ap * up * b * a + ap * b * rr * dp * l * up + b * rr * bp * ap * dp)
 
     def site_env(self, r, c, ub, up, db, dp):
+        """B = (F Mu) (Md G): pair each boundary with its neighbour, then one
+        contraction over (a', b)."""
         a, b = ub[c], ub[c + 1]
         ap, bp = db[c], db[c + 1]
         l, rr, _, _ = self.tdim(r, c)
-        return 2 * (ap * dp * b * rr * bp + a * up * ap * dp * rr * b + l * up * dp * rr * a * ap)
+        return 2 * (ap * l * up * b * a + ap * dp * b * rr * bp + l * up * dp * rr * ap * b)
 
     def pair_flops(self, spins=None, J2=0.5):
         """Two-row sandwiches of one configuration: transfers both ways plus flip ratios."""
