@@ -418,6 +418,226 @@ __device__ void inverse_iteration(const R* t, int n2, R lam, R pivtiny, R* ws, i
 #undef IX
 }
 
+// v[k] for a run-time k
+__device__ __forceinline__ float sel8(const float (&v)[8], int k) {
+  float x = v[0];
+#pragma unroll
+  for (int q = 1; q < 8; ++q) x = k == q ? v[q] : x;
+  return x;
+}
+// column c (run-time index) of a pair-packed 8 x 8 tile
+__device__ __forceinline__ void col_of(const float2 (&a)[8][4], int c, float (&out)[8]) {
+  const int q = c >> 1;
+  const bool hi = c & 1;
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    float2 p = a[r][0];
+#pragma unroll
+    for (int k = 1; k < 4; ++k) p = q == k ? a[r][k] : p;
+    out[r] = hi ? p.y : p.x;
+  }
+}
+// row r (run-time index) of a pair-packed 8 x 8 tile
+__device__ __forceinline__ void row_of(const float2 (&a)[8][4], int r, float (&out)[8]) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    float2 p = a[0][k];
+#pragma unroll
+    for (int rr = 1; rr < 8; ++rr) p = r == rr ? a[rr][k] : p;
+    out[2 * k] = p.x;
+    out[2 * k + 1] = p.y;
+  }
+}
+// Householder bidiagonalisation of an FP32 matrix of at most 128 x 128 held
+// in registers: thread (ti, tj) owns the 8 x 8 tile of rows 8 ti.., columns
+// 8 tj.., with ti = lane % 16 and tj = 2 warp + lane / 16, so the 16 tiles of a
+// tile column sit in one half-warp (column sums are shuffle reductions) and
+// the tiles of a tile row in one lane position of every half-warp.  A tile is
+// kept as column pairs and updated with packed FP32x2 multiply-adds; the
+// active row and column are picked out of the tile by selects (a register
+// array cannot be indexed at run time).  Not inlined: its own register
+// allocation holds the 64-element tile without spilling.  The
+// arithmetic is that of the shared-memory version below (same reflectors,
+// same stored factors); only the order of the partial sums differs.  One
+// column costs three barriers: broadcast of the left reflector, the row norm
+// of the right reflector, and the cross-warp sums of W u.  Warps whose two
+// tile columns lie left of the active column skip the products.  On return W
+// (P x Q, leading dimension ld) holds the unscaled reflectors; t and tau4
+// (tau left, tau right, scale left, scale right, qm apart) are set as by the
+// shared-memory version.
+static __device__ __noinline__ void bidiag_tiles_f32(const float* X, int n, bool tall, int P, int Q, float* W, int ld,
+                                                 float* t, float* tau4, int qm) {
+  __shared__ __align__(16) float zp[kWarps * 128];   // per-warp partial sums of W u
+  __shared__ __align__(16) float vL[128];            // left reflector, by row
+  __shared__ float sc[2 + 16];                       // tau_left, alpha_right, row-norm partials
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, ti = lane & 15;
+  const int tj = warp * 2 + (lane >> 4);
+  const int r0 = ti * 8, c0 = tj * 8;
+  const unsigned hmask = (lane & 16) ? 0xffff0000u : 0x0000ffffu;
+  float2 a[8][4];   // a[r][q] = columns (2q, 2q+1) of row r of the tile
+#pragma unroll
+  for (int r = 0; r < 8; ++r)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int i = r0 + r, c = c0 + 2 * q;
+      float x0 = 0.f, x1 = 0.f;
+      if (i < P) {
+        if (c < Q) x0 = tall ? X[i * n + c] : X[c * n + i];
+        if (c + 1 < Q) x1 = tall ? X[i * n + c + 1] : X[(c + 1) * n + i];
+      }
+      a[r][q] = make_float2(x0, x1);
+    }
+  for (int jb = 0; jb < Q; jb += 8) {
+    const int tb = jb >> 3;   // tile row / column of j
+#pragma unroll 1
+    for (int jj = 0; jj < 8; ++jj) {
+      const int j = jb + jj;
+      if (j < Q) {
+        // ---- left reflector on column j (rows j..P-1), formed by the owning half-warp
+        if (tj == tb) {
+          float col[8];
+          col_of(a, jj, col);
+          float ss = 0.f;
+#pragma unroll
+          for (int r = 0; r < 8; ++r)
+            if (r0 + r > j) ss = fmaf(col[r], col[r], ss);
+#pragma unroll
+          for (int o = 8; o >= 1; o >>= 1) ss += __shfl_xor_sync(hmask, ss, o);
+          const float alpha = __shfl_sync(hmask, sel8(col, jj), (lane & 16) | tb);
+          float tau, scale, beta;
+          householder(alpha, ss, tau, scale, beta);
+#pragma unroll
+          for (int r = 0; r < 8; ++r) {
+            const int i = r0 + r;
+            vL[i] = i == j ? 1.f : (i > j ? scale * col[r] : 0.f);
+          }
+          if (ti == 0) {
+            sc[0] = tau;
+            t[2 * j] = beta;
+            tau4[j] = tau;
+            tau4[2 * qm + j] = scale;
+          }
+        }
+        __syncthreads();
+        if (warp * 16 + 15 > j) {   // some column of this warp lies right of j
+          const float tau = sc[0];
+          float v[8];
+          const float4 v0 = *reinterpret_cast<const float4*>(vL + r0);
+          const float4 v1 = *reinterpret_cast<const float4*>(vL + r0 + 4);
+          v[0] = v0.x; v[1] = v0.y; v[2] = v0.z; v[3] = v0.w;
+          v[4] = v1.x; v[5] = v1.y; v[6] = v1.z; v[7] = v1.w;
+          float2 wc[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            float2 s = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int r = 0; r < 8; ++r) s = __ffma2_rn(make_float2(v[r], v[r]), a[r][q], s);
+            wc[q] = s;
+          }
+#pragma unroll
+          for (int o = 8; o >= 1; o >>= 1)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              wc[q].x += __shfl_xor_sync(0xffffffffu, wc[q].x, o);
+              wc[q].y += __shfl_xor_sync(0xffffffffu, wc[q].y, o);
+            }
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            wc[q].x = (c0 + 2 * q > j) ? -tau * wc[q].x : 0.f;
+            wc[q].y = (c0 + 2 * q + 1 > j) ? -tau * wc[q].y : 0.f;
+          }
+#pragma unroll
+          for (int r = 0; r < 8; ++r)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) a[r][q] = __ffma2_rn(make_float2(v[r], v[r]), wc[q], a[r][q]);
+        }
+        if (j < Q - 1) {
+          // ---- right reflector on row j (columns j+1..Q-1)
+          const int ja = (jj + 1) & 7;       // local column of j+1
+          const int ta = (j + 1) >> 3;       // its tile column
+          float row[8];
+          row_of(a, jj, row);
+          if (ti == tb) {
+            float ss = 0.f;
+#pragma unroll
+            for (int c = 0; c < 8; ++c)
+              if (c0 + c > j + 1) ss = fmaf(row[c], row[c], ss);
+            sc[2 + tj] = ss;
+            if (tj == ta) sc[1] = sel8(row, ja);
+          }
+          __syncthreads();
+          float ssr = 0.f;
+#pragma unroll
+          for (int q = 0; q < 16; ++q) ssr += sc[2 + q];
+          float tr, sr, br;
+          householder(sc[1], ssr, tr, sr, br);
+          if (tid == 0) {
+            t[2 * j + 1] = br;
+            tau4[qm + j] = tr;
+            tau4[3 * qm + j] = sr;
+          }
+          const bool act = warp * 16 + 15 > j;   // warp-uniform: some u entry of this warp is non-zero
+          float2 u[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const float2 x = make_float2(__shfl_sync(0xffffffffu, row[2 * q], (lane & 16) | tb),
+                                         __shfl_sync(0xffffffffu, row[2 * q + 1], (lane & 16) | tb));
+            const int c = c0 + 2 * q;
+            u[q].x = c == j + 1 ? 1.f : (c > j + 1 ? sr * x.x : 0.f);
+            u[q].y = c + 1 == j + 1 ? 1.f : (c + 1 > j + 1 ? sr * x.y : 0.f);
+          }
+          float z[8];
+          if (act) {
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+              float2 s = make_float2(0.f, 0.f);
+#pragma unroll
+              for (int q = 0; q < 4; ++q) s = __ffma2_rn(a[r][q], u[q], s);
+              z[r] = s.x + s.y;
+            }
+#pragma unroll
+            for (int r = 0; r < 8; ++r) z[r] += __shfl_xor_sync(0xffffffffu, z[r], 16);
+          } else {
+#pragma unroll
+            for (int r = 0; r < 8; ++r) z[r] = 0.f;
+          }
+          if (lane < 16) {
+            *reinterpret_cast<float4*>(zp + warp * 128 + r0) = make_float4(z[0], z[1], z[2], z[3]);
+            *reinterpret_cast<float4*>(zp + warp * 128 + r0 + 4) = make_float4(z[4], z[5], z[6], z[7]);
+          }
+          __syncthreads();
+          if (act) {
+#pragma unroll
+            for (int r = 0; r < 8; ++r) z[r] = 0.f;
+#pragma unroll
+            for (int q = 0; q < kWarps; ++q) {
+              const float4 p0 = *reinterpret_cast<const float4*>(zp + q * 128 + r0);
+              const float4 p1 = *reinterpret_cast<const float4*>(zp + q * 128 + r0 + 4);
+              z[0] += p0.x; z[1] += p0.y; z[2] += p0.z; z[3] += p0.w;
+              z[4] += p1.x; z[5] += p1.y; z[6] += p1.z; z[7] += p1.w;
+            }
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+              const float zr = (r0 + r > j) ? -tr * z[r] : 0.f;
+#pragma unroll
+              for (int q = 0; q < 4; ++q) a[r][q] = __ffma2_rn(make_float2(zr, zr), u[q], a[r][q]);
+            }
+          }
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < 8; ++r)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int i = r0 + r, c = c0 + 2 * q;
+      if (i < P && c < Q) W[i * ld + c] = a[r][q].x;
+      if (i < P && c + 1 < Q) W[i * ld + c + 1] = a[r][q].y;
+    }
+  __syncthreads();
+}
+
 // Writes U_K (m x K) through (uo_r, uo_c) and C' = U_K^T X (K x n) through
 // (co_r, co_c).  X is not modified.  K <= min(m, n), K <= 32.
 template <typename R>
@@ -442,157 +662,166 @@ __device__ void cta_topk_left(const R* X, int m, int n, int K, TruncWork<R>& w, 
   const int P = tall ? m : n, Q = tall ? n : m;
   const int ld = w.ldw;
   R* W = w.Wm;
-  for (int e = tid; e < m * n; e += blockDim.x) {
-    const int i = e / n, j = e % n;
-    if (tall) W[i * ld + j] = X[e];
-    else W[j * ld + i] = X[e];
-  }
-  __syncthreads();
   R* tauL = w.tau;
   R* tauR = w.tau + w.Qmax;
   R* red = w.red;
-  // ---------------- bidiagonalisation: W = Q_L B Q_R^T, B upper bidiagonal
-  // Reflectors are kept unscaled in W with their scale factors in sL / sR
-  // (v = scale * stored, implicit 1 on the diagonal / super-diagonal).  The
-  // norm each Householder vector needs is accumulated while the previous
-  // rank-1 update writes those entries, and every thread forms the scalars
-  // itself, so one column costs four barriers.
-  R* wv = w.wv;
-  R* sL = w.tau + 2 * w.Qmax;        // left scale factors (t2 is filled later)
-  R* sR = sL + w.Qmax;
-  R* part = red + 40;                // per-warp partial norms (8)
-  {
-    R ss = R(0);
-    for (int i = 1 + tid; i < P; i += blockDim.x) ss += W[i * ld] * W[i * ld];
-    ss = block_sum(ss, red + 16);
-    if (tid < kWarps) part[tid] = tid == 0 ? ss : R(0);
-    __syncthreads();
-  }
-  for (int j = 0; j < Q; ++j) {
-    // -- left reflector on column j (rows j..P-1); its norm is in part[]
-    R colnorm = R(0);
-    for (int q = 0; q < kWarps; ++q) colnorm += part[q];
-    R tau, scale, beta;
-    householder(W[j * ld + j], colnorm, tau, scale, beta);
-    if (tid == 0) {
-      w.t[2 * j] = beta;
-      tauL[j] = tau;
-      sL[j] = scale;
+  bool tiled = false;
+  if constexpr (sizeof(R) == 4) {
+    if (P > 32 && P <= 128) {   // below 33 rows the shared-memory version is as fast
+      bidiag_tiles_f32(X, n, tall, P, Q, W, ld, w.t, w.tau, w.Qmax);
+      tiled = true;
     }
-    const int ncol = Q - j - 1;
-    R rownorm = R(0);                // squared norm of row j beyond j+1 after the left update
-    if (tau != R(0) && ncol > 0) {
-      // wv[c] = tau * (W[j][c] + scale * sum_{i>j} W[i][j] W[i][c])
-      int tpc = kThreads / ncol;
-      tpc = tpc >= 32 ? 32 : tpc >= 16 ? 16 : tpc >= 8 ? 8 : tpc >= 4 ? 4 : tpc >= 2 ? 2 : 1;
-      const int cpr = kThreads / tpc;
-      for (int cb = 0; cb < ncol; cb += cpr) {
-        const int cl = cb + tid / tpc, gl = tid % tpc;
-        const bool act = cl < ncol;
-        const int c = j + 1 + (act ? cl : 0);
-        R s0 = R(0), s1 = R(0), s2 = R(0), s3 = R(0);
-        int i = j + 1 + gl;
-        for (; i + 3 * tpc < P; i += 4 * tpc) {
-          s0 += W[i * ld + j] * W[i * ld + c];
-          s1 += W[(i + tpc) * ld + j] * W[(i + tpc) * ld + c];
-          s2 += W[(i + 2 * tpc) * ld + j] * W[(i + 2 * tpc) * ld + c];
-          s3 += W[(i + 3 * tpc) * ld + j] * W[(i + 3 * tpc) * ld + c];
-        }
-        for (; i < P; i += tpc) s0 += W[i * ld + j] * W[i * ld + c];
-        const R sacc = warp_sum((s0 + s1) + (s2 + s3), tpc);
-        if (act && gl == 0) wv[c] = tau * (W[j * ld + c] + scale * sacc);
-      }
+  }
+  if (!tiled) {
+    for (int e = tid; e < m * n; e += blockDim.x) {
+      const int i = e / n, j = e % n;
+      if (tall) W[i * ld + j] = X[e];
+      else W[j * ld + i] = X[e];
+    }
+    __syncthreads();
+    // ---------------- bidiagonalisation: W = Q_L B Q_R^T, B upper bidiagonal
+    // Reflectors are kept unscaled in W with their scale factors in sL / sR
+    // (v = scale * stored, implicit 1 on the diagonal / super-diagonal).  The
+    // norm each Householder vector needs is accumulated while the previous
+    // rank-1 update writes those entries, and every thread forms the scalars
+    // itself, so one column costs four barriers.
+    R* wv = w.wv;
+    R* sL = w.tau + 2 * w.Qmax;        // left scale factors (t2 is filled later)
+    R* sR = sL + w.Qmax;
+    R* part = red + 40;                // per-warp partial norms (8)
+    {
+      R ss = R(0);
+      for (int i = 1 + tid; i < P; i += blockDim.x) ss += W[i * ld] * W[i * ld];
+      ss = block_sum(ss, red + 16);
+      if (tid < kWarps) part[tid] = tid == 0 ? ss : R(0);
       __syncthreads();
-      // W[i][c] -= wv[c] v_i for i >= j, c > j; warp 0 takes row j and its norm
-      for (int i = j + warp; i < P; i += kWarps) {
-        const R v = i == j ? R(1) : scale * W[i * ld + j];
-        R rn = R(0);
-        for (int c = j + 1 + lane; c < Q; c += 32) {
-          const R x = W[i * ld + c] - wv[c] * v;
-          W[i * ld + c] = x;
-          if (c >= j + 2) rn += x * x;
+    }
+    for (int j = 0; j < Q; ++j) {
+      // -- left reflector on column j (rows j..P-1); its norm is in part[]
+      R colnorm = R(0);
+      for (int q = 0; q < kWarps; ++q) colnorm += part[q];
+      R tau, scale, beta;
+      householder(W[j * ld + j], colnorm, tau, scale, beta);
+      if (tid == 0) {
+        w.t[2 * j] = beta;
+        tauL[j] = tau;
+        sL[j] = scale;
+      }
+      const int ncol = Q - j - 1;
+      R rownorm = R(0);                // squared norm of row j beyond j+1 after the left update
+      if (tau != R(0) && ncol > 0) {
+        // wv[c] = tau * (W[j][c] + scale * sum_{i>j} W[i][j] W[i][c])
+        int tpc = kThreads / ncol;
+        tpc = tpc >= 32 ? 32 : tpc >= 16 ? 16 : tpc >= 8 ? 8 : tpc >= 4 ? 4 : tpc >= 2 ? 2 : 1;
+        const int cpr = kThreads / tpc;
+        for (int cb = 0; cb < ncol; cb += cpr) {
+          const int cl = cb + tid / tpc, gl = tid % tpc;
+          const bool act = cl < ncol;
+          const int c = j + 1 + (act ? cl : 0);
+          R s0 = R(0), s1 = R(0), s2 = R(0), s3 = R(0);
+          int i = j + 1 + gl;
+          for (; i + 3 * tpc < P; i += 4 * tpc) {
+            s0 += W[i * ld + j] * W[i * ld + c];
+            s1 += W[(i + tpc) * ld + j] * W[(i + tpc) * ld + c];
+            s2 += W[(i + 2 * tpc) * ld + j] * W[(i + 2 * tpc) * ld + c];
+            s3 += W[(i + 3 * tpc) * ld + j] * W[(i + 3 * tpc) * ld + c];
+          }
+          for (; i < P; i += tpc) s0 += W[i * ld + j] * W[i * ld + c];
+          const R sacc = warp_sum((s0 + s1) + (s2 + s3), tpc);
+          if (act && gl == 0) wv[c] = tau * (W[j * ld + c] + scale * sacc);
         }
-        if (i == j) {
+        __syncthreads();
+        // W[i][c] -= wv[c] v_i for i >= j, c > j; warp 0 takes row j and its norm
+        for (int i = j + warp; i < P; i += kWarps) {
+          const R v = i == j ? R(1) : scale * W[i * ld + j];
+          R rn = R(0);
+          for (int c = j + 1 + lane; c < Q; c += 32) {
+            const R x = W[i * ld + c] - wv[c] * v;
+            W[i * ld + c] = x;
+            if (c >= j + 2) rn += x * x;
+          }
+          if (i == j) {
+            rn = warp_sum(rn);
+            if (lane == 0) red[5] = rn;
+          }
+        }
+        __syncthreads();
+        rownorm = red[5];
+      } else if (ncol > 0) {
+        if (warp == 0) {
+          R rn = R(0);
+          for (int c = j + 2 + lane; c < Q; c += 32) rn += W[j * ld + c] * W[j * ld + c];
           rn = warp_sum(rn);
           if (lane == 0) red[5] = rn;
         }
-      }
-      __syncthreads();
-      rownorm = red[5];
-    } else if (ncol > 0) {
-      if (warp == 0) {
-        R rn = R(0);
-        for (int c = j + 2 + lane; c < Q; c += 32) rn += W[j * ld + c] * W[j * ld + c];
-        rn = warp_sum(rn);
-        if (lane == 0) red[5] = rn;
-      }
-      __syncthreads();
-      rownorm = red[5];
-    }
-    if (j < Q - 1) {
-      // -- right reflector on row j (columns j+1..Q-1)
-      R tr, sr, br;
-      householder(W[j * ld + j + 1], rownorm, tr, sr, br);
-      if (tid == 0) {
-        w.t[2 * j + 1] = br;
-        tauR[j] = tr;
-        sR[j] = sr;
-      }
-      const int nrow = P - j - 1;
-      if (tr != R(0)) {
-        // wv[i] = tr * (W[i][j+1] + sr * sum_{c>j+1} W[i][c] W[j][c])
-        int tpc = kThreads / nrow;
-        tpc = tpc >= 32 ? 32 : tpc >= 16 ? 16 : tpc >= 8 ? 8 : tpc >= 4 ? 4 : tpc >= 2 ? 2 : 1;
-        const int rpr = kThreads / tpc;
-        for (int rb = 0; rb < nrow; rb += rpr) {
-          const int rl = rb + tid / tpc, gl = tid % tpc;
-          const bool act = rl < nrow;
-          const int i = j + 1 + (act ? rl : 0);
-          R s0 = R(0), s1 = R(0), s2 = R(0), s3 = R(0);
-          int c = j + 2 + gl;
-          for (; c + 3 * tpc < Q; c += 4 * tpc) {
-            s0 += W[i * ld + c] * W[j * ld + c];
-            s1 += W[i * ld + c + tpc] * W[j * ld + c + tpc];
-            s2 += W[i * ld + c + 2 * tpc] * W[j * ld + c + 2 * tpc];
-            s3 += W[i * ld + c + 3 * tpc] * W[j * ld + c + 3 * tpc];
-          }
-          for (; c < Q; c += tpc) s0 += W[i * ld + c] * W[j * ld + c];
-          const R sacc = warp_sum((s0 + s1) + (s2 + s3), tpc);
-          if (act && gl == 0) wv[i] = tr * (W[i * ld + j + 1] + sr * sacc);
-        }
         __syncthreads();
-        // W[i][c] -= wv[i] v'_c for i > j, c > j; lane 0 of each warp sums column j+1 below row j+1
-        R vl[8];
-#pragma unroll
-        for (int t = 0; t < 8; ++t) {
-          const int c = j + 1 + lane + 32 * t;
-          vl[t] = c == j + 1 ? R(1) : (c < Q ? sr * W[j * ld + c] : R(0));
+        rownorm = red[5];
+      }
+      if (j < Q - 1) {
+        // -- right reflector on row j (columns j+1..Q-1)
+        R tr, sr, br;
+        householder(W[j * ld + j + 1], rownorm, tr, sr, br);
+        if (tid == 0) {
+          w.t[2 * j + 1] = br;
+          tauR[j] = tr;
+          sR[j] = sr;
         }
-        R cn = R(0);
-        for (int i = j + 1 + warp; i < P; i += kWarps) {
-          const R wi = wv[i];
-#pragma unroll
+        const int nrow = P - j - 1;
+        if (tr != R(0)) {
+          // wv[i] = tr * (W[i][j+1] + sr * sum_{c>j+1} W[i][c] W[j][c])
+          int tpc = kThreads / nrow;
+          tpc = tpc >= 32 ? 32 : tpc >= 16 ? 16 : tpc >= 8 ? 8 : tpc >= 4 ? 4 : tpc >= 2 ? 2 : 1;
+          const int rpr = kThreads / tpc;
+          for (int rb = 0; rb < nrow; rb += rpr) {
+            const int rl = rb + tid / tpc, gl = tid % tpc;
+            const bool act = rl < nrow;
+            const int i = j + 1 + (act ? rl : 0);
+            R s0 = R(0), s1 = R(0), s2 = R(0), s3 = R(0);
+            int c = j + 2 + gl;
+            for (; c + 3 * tpc < Q; c += 4 * tpc) {
+              s0 += W[i * ld + c] * W[j * ld + c];
+              s1 += W[i * ld + c + tpc] * W[j * ld + c + tpc];
+              s2 += W[i * ld + c + 2 * tpc] * W[j * ld + c + 2 * tpc];
+              s3 += W[i * ld + c + 3 * tpc] * W[j * ld + c + 3 * tpc];
+            }
+            for (; c < Q; c += tpc) s0 += W[i * ld + c] * W[j * ld + c];
+            const R sacc = warp_sum((s0 + s1) + (s2 + s3), tpc);
+            if (act && gl == 0) wv[i] = tr * (W[i * ld + j + 1] + sr * sacc);
+          }
+          __syncthreads();
+          // W[i][c] -= wv[i] v'_c for i > j, c > j; lane 0 of each warp sums column j+1 below row j+1
+          R vl[8];
+  #pragma unroll
           for (int t = 0; t < 8; ++t) {
             const int c = j + 1 + lane + 32 * t;
-            if (c < Q) {
-              const R x = W[i * ld + c] - wi * vl[t];
-              W[i * ld + c] = x;
-              if (t == 0 && lane == 0 && i > j + 1) cn += x * x;
+            vl[t] = c == j + 1 ? R(1) : (c < Q ? sr * W[j * ld + c] : R(0));
+          }
+          R cn = R(0);
+          for (int i = j + 1 + warp; i < P; i += kWarps) {
+            const R wi = wv[i];
+  #pragma unroll
+            for (int t = 0; t < 8; ++t) {
+              const int c = j + 1 + lane + 32 * t;
+              if (c < Q) {
+                const R x = W[i * ld + c] - wi * vl[t];
+                W[i * ld + c] = x;
+                if (t == 0 && lane == 0 && i > j + 1) cn += x * x;
+              }
             }
           }
+          if (lane == 0) part[warp] = cn;
+          __syncthreads();
+        } else {
+          // no right update: column j+1's norm below row j+1 as it stands
+          R cn = R(0);
+          for (int i = j + 2 + tid; i < P; i += blockDim.x) cn += W[i * ld + j + 1] * W[i * ld + j + 1];
+          cn = block_sum(cn, red + 16);
+          if (tid < kWarps) part[tid] = tid == 0 ? cn : R(0);
+          __syncthreads();
         }
-        if (lane == 0) part[warp] = cn;
-        __syncthreads();
-      } else {
-        // no right update: column j+1's norm below row j+1 as it stands
-        R cn = R(0);
-        for (int i = j + 2 + tid; i < P; i += blockDim.x) cn += W[i * ld + j + 1] * W[i * ld + j + 1];
-        cn = block_sum(cn, red + 16);
-        if (tid < kWarps) part[tid] = tid == 0 ? cn : R(0);
-        __syncthreads();
       }
     }
-  }
+  }   // !tiled
   PEPS_PHASE(1);
   // ---------------- Sturm bisection for the K largest singular values
   const int n2 = 2 * Q;
