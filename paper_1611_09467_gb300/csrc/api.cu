@@ -529,7 +529,7 @@ const char* peps_last_error(void) { return g_err.c_str(); }
 peps_status peps_create(const peps_params* p, const double* A_host, void* stream, peps_ctx** out) {
   g_err.clear();
   if (!p || !A_host || !out) return fail(PEPS_EINVAL, "null argument");
-  if (p->Lx < 2 || p->Ly < 2 || p->Lx > 64 || p->Ly > 64) return fail(PEPS_EINVAL, "Lx, Ly must be in [2, 64]");
+  if (p->Lx < 2 || p->Ly < 2 || p->Lx > kMaxL || p->Ly > kMaxL) return fail(PEPS_EINVAL, "Lx, Ly must be in [2, 64]");
   if ((long)p->Lx * p->Ly > 64L * kMaxWords) return fail(PEPS_EINVAL, "too many sites");
   if (p->d != 2) return fail(PEPS_EINVAL, "d must be 2");
   if (p->D < 1 || p->D > 16) return fail(PEPS_EINVAL, "D must be in [1, 16]");

@@ -58,6 +58,64 @@ __device__ R block_sum(R v, R* red) {
   return s;
 }
 
+// Block-wide maximum; same contract as block_sum.
+template <typename R>
+__device__ R block_max(R v, R* red) {
+  v = warp_max(v);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  R s = red[0];
+  for (int i = 1; i < kWarps; ++i) s = fmax(s, red[i]);
+  __syncthreads();
+  return s;
+}
+
+// Power-of-two renormalisation of the transfer vectors of the sandwiches.
+// A sandwich value between unit-norm environments can fall far below the
+// FP32 range (it is psi divided by the norms of all other rows), so every
+// stored transfer is scaled by an exact power of two and its exponent is
+// carried beside it; ratios and Delta add the exponents back in FP64.
+// pow2_exponent(m) = floor(log2 m) read from the bits of m, clamped so that
+// 2^-e is a normal number; 0 for m = 0 or m not finite.
+__device__ __forceinline__ int pow2_exponent(float m) {
+  const int ef = (int)((__float_as_uint(m) >> 23) & 0xffu);
+  if (!(m > 0.f) || ef == 0xff) return 0;
+  const int e = ef - 127;
+  return e < -126 ? -126 : (e > 126 ? 126 : e);
+}
+__device__ __forceinline__ int pow2_exponent(double m) {
+  const int ef = (int)((__double_as_longlong(m) >> 52) & 0x7ffll);
+  if (!(m > 0.0) || ef == 0x7ff) return 0;
+  const int e = ef - 1023;
+  return e < -1022 ? -1022 : (e > 1022 ? 1022 : e);
+}
+// 2^e for e in the clamped range of pow2_exponent
+template <typename R>
+__device__ __forceinline__ R pow2(int e);
+template <>
+__device__ __forceinline__ float pow2<float>(int e) { return __uint_as_float((unsigned)(e + 127) << 23); }
+template <>
+__device__ __forceinline__ double pow2<double>(int e) {
+  return __longlong_as_double((long long)(e + 1023) << 52);
+}
+
+// Scales x[0..n) in place by 2^-e, e = pow2_exponent(max |x|), and returns e.
+// x must be complete (written before a barrier); ends with a barrier.
+template <typename R>
+__device__ int normalize_pow2(R* x, int n, R* red) {
+  R m = R(0);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) m = fmax(m, fabs(x[i]));
+  m = block_max(m, red);
+  const int e = pow2_exponent(m);
+  if (e != 0) {
+    const R sc = pow2<R>(-e);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] *= sc;
+  }
+  __syncthreads();
+  return e;
+}
+
 // ------------------------------------------------------------- CTA GEMM
 // Shared-memory tiled GEMM over the index maps of a descriptor (see
 // contract.cuh).  Per output tile (TM x TN) the K range is walked in chunks
@@ -66,13 +124,18 @@ __device__ R block_sum(R v, R* red) {
 // MT x NT micro-tile in registers.  The CTA tile shape follows N (the
 // contraction steps have N in {16, 32, 64, 128, 256+}).  Shared memory:
 // kGemmSmemReals reals + kGemmSmemInts ints supplied by the caller.
+// A and B are often written earlier by the same kernel (carries, blocks,
+// singular vectors), so they are not declared __restrict__: that would let
+// the compiler read them through the non-coherent read-only path, which is
+// only valid for data that no thread writes while the kernel runs.  The same
+// holds for the transfer inputs of the fused steps.
 constexpr int kGemmTK = 16;
 constexpr int kMaxK = 1024;
 constexpr int kGemmSmemReals = kGemmTK * (512 + 16);
 constexpr int kGemmSmemInts = 2 * kMaxK + 2 * 512 + 2 * 256;
 
 template <typename R, int TM, int TN, int MT, int NT>
-__device__ __noinline__ void gemm_tiles(const GemmDesc& g, const R* __restrict__ A, const R* __restrict__ B,
+__device__ __noinline__ void gemm_tiles(const GemmDesc& g, const R* A, const R* B,
                                         R* __restrict__ C, bool accumulate, R* sm, int* ism) {
   constexpr int TK = kGemmTK;
   constexpr int GX = TN / NT, GY = TM / MT;
@@ -161,7 +224,7 @@ __device__ __noinline__ void gemm_tiles(const GemmDesc& g, const R* __restrict__
 // C (+)= A B for a descriptor; the whole CTA takes part and the call ends
 // with a barrier.  `sm`/`ism` point to the GEMM's shared-memory scratch.
 template <typename R>
-__device__ void cta_gemm(const GemmDesc& g, const R* __restrict__ A, const R* __restrict__ B, R* __restrict__ C,
+__device__ void cta_gemm(const GemmDesc& g, const R* A, const R* B, R* __restrict__ C,
                          bool accumulate, R* sm, int* ism) {
   if (g.N >= 256 && g.M <= 32) gemm_tiles<R, 16, 256, 4, 4>(g, A, B, C, accumulate, sm, ism);
   else if (g.N >= 128) gemm_tiles<R, 64, 128, 4, 8>(g, A, B, C, accumulate, sm, ism);

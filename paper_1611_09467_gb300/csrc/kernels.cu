@@ -377,23 +377,29 @@ __global__ void __launch_bounds__(kThreads) k_row(KArgs<R> a) {
   R* Bb = p; p += D4;
   R* t0 = p; p += tmp_elems(g);
   R* t1 = p;
+  __shared__ int eG[kMaxL + 1];   // G_c is stored scaled by 2^-eG[c]
   for (int item = blockIdx.x; item < a.n * Ly; item += gridDim.x) {
     const int cfg = item / Ly, r = item % Ly;
     __syncthreads();
     for (int i = threadIdx.x; i < g.nwords; i += blockDim.x) sp[i] = a.S[(size_t)cfg * g.nwords + i];
     for (int e = threadIdx.x; e < envT; e += blockDim.x) Gb[(size_t)Lx * envT + e] = a.triv_t1[e];
+    if (threadIdx.x == 0) eG[Lx] = 0;
     __syncthreads();
     const R* Mu = r == 0 ? a.triv_mps : a.envU + ((size_t)cfg * Ly + (r - 1)) * Lx * envT;
     const R* Md = r == Ly - 1 ? a.triv_mps : a.envL + ((size_t)cfg * Ly + (r + 1)) * Lx * envT;
+    int eacc = 0;
     for (int c = Lx - 1; c >= 0; --c) {
       const int site = r * Lx + c;
       run_op<R>(OP_COL1_RIGHT, D, Dc, Gb + (size_t)(c + 1) * envT, Mu + (size_t)c * envT,
                 tptr(a, site, spin_of(sp, site)), Md + (size_t)c * envT, nullptr, Gb + (size_t)c * envT, t0, t1, gsm, gism);
+      eacc += normalize_pow2(Gb + (size_t)c * envT, envT, red);
+      if (threadIdx.x == 0) eG[c] = eacc;
     }
     const R W = Gb[0];
     const bool ok = W != R(0);
     double eh = 0.0;
     const R* F = a.triv_t1;
+    int eF = 0;   // F is stored scaled by 2^-eF
     R* Fn = F0;
     for (int c = 0; c < Lx; ++c) {
       const int site = r * Lx + c;
@@ -402,7 +408,7 @@ __global__ void __launch_bounds__(kThreads) k_row(KArgs<R> a) {
         run_op<R>(OP_SITE_ENV, D, Dc, F, Mu + (size_t)c * envT, Md + (size_t)c * envT,
                   Gb + (size_t)(c + 1) * envT, nullptr, Bb, t0, t1, gsm, gism);
         R* Oo = a.O + ((size_t)cfg * g.N + site) * D4;
-        const R inv = ok ? R(1) / W : R(0);
+        const R inv = ok ? (R)ldexp(1.0 / (double)W, eF + eG[c + 1] - eG[0]) : R(0);
         for (int e = threadIdx.x; e < D4; e += blockDim.x) Oo[e] = Bb[e] * inv;
       }
       if (c < Lx - 1) {
@@ -410,13 +416,15 @@ __global__ void __launch_bounds__(kThreads) k_row(KArgs<R> a) {
         if (s != s2) {
           run_op<R>(OP_COL1_LEFT, D, Dc, F, Mu + (size_t)c * envT, tptr(a, site, s2), Md + (size_t)c * envT,
                     nullptr, X1, t0, t1, gsm, gism);
+          const int eX = normalize_pow2(X1, envT, red);
           run_op<R>(OP_COL1_LEFT, D, Dc, X1, Mu + (size_t)(c + 1) * envT, tptr(a, site + 1, s),
                     Md + (size_t)(c + 1) * envT, nullptr, X2, t0, t1, gsm, gism);
           const R wp = block_dot(X2, Gb + (size_t)(c + 2) * envT, envT, red);
-          if (ok) eh += 0.5 * g.J1 * ((double)wp / (double)W);
+          if (ok) eh += 0.5 * g.J1 * ldexp((double)wp / (double)W, eF + eX + eG[c + 2] - eG[0]);
         }
         run_op<R>(OP_COL1_LEFT, D, Dc, F, Mu + (size_t)c * envT, tptr(a, site, s), Md + (size_t)c * envT,
                   nullptr, Fn, t0, t1, gsm, gism);
+        eF += normalize_pow2(Fn, envT, red);
         F = Fn;
         Fn = (Fn == F0) ? F1 : F0;
       }
@@ -446,23 +454,30 @@ __global__ void __launch_bounds__(kThreads) k_row_fused(KArgs<R> a) {
   R* F0 = p; p += envT;
   R* F1 = p; p += envT;
   R* X1 = p;
+  __shared__ int eG[kMaxL + 1];   // G_c is stored scaled by 2^-eG[c]
   for (int item = blockIdx.x; item < a.n * Ly; item += gridDim.x) {
     const int cfg = item / Ly, r = item % Ly;
     __syncthreads();
     for (int i = threadIdx.x; i < g.nwords; i += blockDim.x) sp[i] = a.S[(size_t)cfg * g.nwords + i];
     for (int e = threadIdx.x; e < envT; e += blockDim.x) Gb[(size_t)Lx * envT + e] = a.triv_t1[e];
+    if (threadIdx.x == 0) eG[Lx] = 0;
     __syncthreads();
     const R* Mu = r == 0 ? a.triv_mps : a.envU + ((size_t)cfg * Ly + (r - 1)) * Lx * envT;
     const R* Md = r == Ly - 1 ? a.triv_mps : a.envL + ((size_t)cfg * Ly + (r + 1)) * Lx * envT;
+    int eacc = 0;
     for (int c = Lx - 1; c >= 0; --c) {
       const int site = r * Lx + c;
+      int e = 0;
       row_step_fused<R, D, Dc>(true, Gb + (size_t)(c + 1) * envT, Gb + (size_t)c * envT, Mu + (size_t)c * envT,
-                               tptr(a, site, spin_of(sp, site)), Md + (size_t)c * envT, nullptr, sm, red);
+                               tptr(a, site, spin_of(sp, site)), Md + (size_t)c * envT, nullptr, sm, red, &e);
+      eacc += e;
+      if (threadIdx.x == 0) eG[c] = eacc;
     }
     const R W = Gb[0];
     const bool ok = W != R(0);
     double eh = 0.0;
     const R* F = a.triv_t1;
+    int eF = 0;   // F is stored scaled by 2^-eF
     R* Fn = F0;
     for (int c = 0; c < Lx; ++c) {
       const int site = r * Lx + c;
@@ -470,17 +485,21 @@ __global__ void __launch_bounds__(kThreads) k_row_fused(KArgs<R> a) {
       const R* Muc = Mu + (size_t)c * envT;
       const R* Mdc = Md + (size_t)c * envT;
       if (a.O != nullptr)
-        site_env_fused<R, D, Dc>(F, Muc, Mdc, Gb + (size_t)(c + 1) * envT, ok ? R(1) / W : R(0),
+        site_env_fused<R, D, Dc>(F, Muc, Mdc, Gb + (size_t)(c + 1) * envT,
+                                 ok ? (R)ldexp(1.0 / (double)W, eF + eG[c + 1] - eG[0]) : R(0),
                                  a.O + ((size_t)cfg * g.N + site) * D4, sm);
       if (c < Lx - 1) {
         const int s2 = spin_of(sp, site + 1);
         if (s != s2) {
-          row_step_fused<R, D, Dc>(false, F, X1, Muc, tptr(a, site, s2), Mdc, nullptr, sm, red);
+          int eX = 0;
+          row_step_fused<R, D, Dc>(false, F, X1, Muc, tptr(a, site, s2), Mdc, nullptr, sm, red, &eX);
           const R wp = row_step_fused<R, D, Dc>(false, X1, nullptr, Mu + (size_t)(c + 1) * envT, tptr(a, site + 1, s),
                                                 Md + (size_t)(c + 1) * envT, Gb + (size_t)(c + 2) * envT, sm, red);
-          if (ok) eh += 0.5 * g.J1 * ((double)wp / (double)W);
+          if (ok) eh += 0.5 * g.J1 * ldexp((double)wp / (double)W, eF + eX + eG[c + 2] - eG[0]);
         }
-        row_step_fused<R, D, Dc>(false, F, Fn, Muc, tptr(a, site, s), Mdc, nullptr, sm, red);
+        int e1 = 0;
+        row_step_fused<R, D, Dc>(false, F, Fn, Muc, tptr(a, site, s), Mdc, nullptr, sm, red, &e1);
+        eF += e1;
         F = Fn;
         Fn = (Fn == F0) ? F1 : F0;
       }
@@ -514,24 +533,30 @@ __global__ void __launch_bounds__(kThreads) k_pair(KArgs<R> a) {
   R* t0 = p; p += tmp_elems(g);
   R* t1 = p;
   const int npairs = Ly - 1;
+  __shared__ int eH[kMaxL + 1];   // H_c is stored scaled by 2^-eH[c]
   for (int item = blockIdx.x; item < a.n * npairs; item += gridDim.x) {
     const int cfg = item / npairs, r = item % npairs;
     __syncthreads();
     for (int i = threadIdx.x; i < g.nwords; i += blockDim.x) sp[i] = a.S[(size_t)cfg * g.nwords + i];
     for (int e = threadIdx.x; e < envT2; e += blockDim.x) Hb[(size_t)Lx * envT2 + e] = a.triv_t2[e];
+    if (threadIdx.x == 0) eH[Lx] = 0;
     __syncthreads();
     const R* Mu = r == 0 ? a.triv_mps : a.envU + ((size_t)cfg * Ly + (r - 1)) * Lx * envT;
     const R* Md = r + 2 > Ly - 1 ? a.triv_mps : a.envL + ((size_t)cfg * Ly + (r + 2)) * Lx * envT;
+    int eacc = 0;
     for (int c = Lx - 1; c >= 0; --c) {
       const int s1 = r * Lx + c, s2 = (r + 1) * Lx + c;
       run_op<R>(OP_COL2_RIGHT, D, Dc, Hb + (size_t)(c + 1) * envT2, Mu + (size_t)c * envT,
                 tptr(a, s1, spin_of(sp, s1)), tptr(a, s2, spin_of(sp, s2)), Md + (size_t)c * envT,
                 Hb + (size_t)c * envT2, t0, t1, gsm, gism);
+      eacc += normalize_pow2(Hb + (size_t)c * envT2, envT2, red);
+      if (threadIdx.x == 0) eH[c] = eacc;
     }
     const R W = Hb[0];
     const bool ok = W != R(0);
     double ev = 0.0;
     const R* E = a.triv_t2;
+    int eE = 0;   // E is stored scaled by 2^-eE
     R* En = E0;
     for (int c = 0; c < Lx; ++c) {
       const int i1 = r * Lx + c, i2 = (r + 1) * Lx + c;
@@ -541,7 +566,7 @@ __global__ void __launch_bounds__(kThreads) k_pair(KArgs<R> a) {
       if (a1 != a2) {  // vertical pair (r,c)-(r+1,c)
         run_op<R>(OP_COL2_LEFT, D, Dc, E, Muc, tptr(a, i1, a2), tptr(a, i2, a1), Mdc, X1, t0, t1, gsm, gism);
         const R wp = block_dot(X1, Hb + (size_t)(c + 1) * envT2, envT2, red);
-        if (ok) ev += 0.5 * g.J1 * ((double)wp / (double)W);
+        if (ok) ev += 0.5 * g.J1 * ldexp((double)wp / (double)W, eE + eH[c + 1] - eH[0]);
       }
       if (c < Lx - 1 && g.J2 != 0.0) {
         const int j1 = i1 + 1, j2 = i2 + 1;
@@ -550,19 +575,22 @@ __global__ void __launch_bounds__(kThreads) k_pair(KArgs<R> a) {
         const R* Mdn = Md + (size_t)(c + 1) * envT;
         if (a1 != b2) {  // diagonal (r,c)-(r+1,c+1)
           run_op<R>(OP_COL2_LEFT, D, Dc, E, Muc, tptr(a, i1, b2), tptr(a, i2, a2), Mdc, X1, t0, t1, gsm, gism);
+          const int eX = normalize_pow2(X1, envT2, red);
           run_op<R>(OP_COL2_LEFT, D, Dc, X1, Mun, tptr(a, j1, b1), tptr(a, j2, a1), Mdn, X2, t0, t1, gsm, gism);
           const R wp = block_dot(X2, Hb + (size_t)(c + 2) * envT2, envT2, red);
-          if (ok) ev += 0.5 * g.J2 * ((double)wp / (double)W);
+          if (ok) ev += 0.5 * g.J2 * ldexp((double)wp / (double)W, eE + eX + eH[c + 2] - eH[0]);
         }
         if (b1 != a2) {  // anti-diagonal (r,c+1)-(r+1,c)
           run_op<R>(OP_COL2_LEFT, D, Dc, E, Muc, tptr(a, i1, a1), tptr(a, i2, b1), Mdc, X1, t0, t1, gsm, gism);
+          const int eX = normalize_pow2(X1, envT2, red);
           run_op<R>(OP_COL2_LEFT, D, Dc, X1, Mun, tptr(a, j1, a2), tptr(a, j2, b2), Mdn, X2, t0, t1, gsm, gism);
           const R wp = block_dot(X2, Hb + (size_t)(c + 2) * envT2, envT2, red);
-          if (ok) ev += 0.5 * g.J2 * ((double)wp / (double)W);
+          if (ok) ev += 0.5 * g.J2 * ldexp((double)wp / (double)W, eE + eX + eH[c + 2] - eH[0]);
         }
       }
       if (c < Lx - 1) {
         run_op<R>(OP_COL2_LEFT, D, Dc, E, Muc, tptr(a, i1, a1), tptr(a, i2, a2), Mdc, En, t0, t1, gsm, gism);
+        eE += normalize_pow2(En, envT2, red);
         E = En;
         En = (En == E0) ? E1 : E0;
       }
@@ -592,24 +620,31 @@ __global__ void __launch_bounds__(kThreads) k_pair_fused(KArgs<R> a) {
   R* E1 = p; p += envT2;
   R* X1 = p;
   const int npairs = Ly - 1;
+  __shared__ int eH[kMaxL + 1];   // H_c is stored scaled by 2^-eH[c]
   for (int item = blockIdx.x; item < a.n * npairs; item += gridDim.x) {
     const int cfg = item / npairs, r = item % npairs;
     __syncthreads();
     for (int i = threadIdx.x; i < g.nwords; i += blockDim.x) sp[i] = a.S[(size_t)cfg * g.nwords + i];
     for (int e = threadIdx.x; e < envT2; e += blockDim.x) Hb[(size_t)Lx * envT2 + e] = a.triv_t2[e];
+    if (threadIdx.x == 0) eH[Lx] = 0;
     __syncthreads();
     const R* Mu = r == 0 ? a.triv_mps : a.envU + ((size_t)cfg * Ly + (r - 1)) * Lx * envT;
     const R* Md = r + 2 > Ly - 1 ? a.triv_mps : a.envL + ((size_t)cfg * Ly + (r + 2)) * Lx * envT;
+    int eacc = 0;
     for (int c = Lx - 1; c >= 0; --c) {
       const int s1 = r * Lx + c, s2 = (r + 1) * Lx + c;
+      int e = 0;
       pair_step_fused<R, D, Dc>(true, Hb + (size_t)(c + 1) * envT2, Hb + (size_t)c * envT2, Mu + (size_t)c * envT,
                                 tptr(a, s1, spin_of(sp, s1)), tptr(a, s2, spin_of(sp, s2)), Md + (size_t)c * envT,
-                                nullptr, sm, red);
+                                nullptr, sm, red, &e);
+      eacc += e;
+      if (threadIdx.x == 0) eH[c] = eacc;
     }
     const R W = Hb[0];
     const bool ok = W != R(0);
     double ev = 0.0;
     const R* E = a.triv_t2;
+    int eE = 0;   // E is stored scaled by 2^-eE
     R* En = E0;
     for (int c = 0; c < Lx; ++c) {
       const int i1 = r * Lx + c, i2 = (r + 1) * Lx + c;
@@ -619,7 +654,7 @@ __global__ void __launch_bounds__(kThreads) k_pair_fused(KArgs<R> a) {
       if (a1 != a2) {  // vertical pair (r,c)-(r+1,c)
         const R wp = pair_step_fused<R, D, Dc>(false, E, nullptr, Muc, tptr(a, i1, a2), tptr(a, i2, a1), Mdc,
                                                Hb + (size_t)(c + 1) * envT2, sm, red);
-        if (ok) ev += 0.5 * g.J1 * ((double)wp / (double)W);
+        if (ok) ev += 0.5 * g.J1 * ldexp((double)wp / (double)W, eE + eH[c + 1] - eH[0]);
       }
       if (c < Lx - 1 && g.J2 != 0.0) {
         const int j1 = i1 + 1, j2 = i2 + 1;
@@ -627,20 +662,24 @@ __global__ void __launch_bounds__(kThreads) k_pair_fused(KArgs<R> a) {
         const R* Mun = Mu + (size_t)(c + 1) * envT;
         const R* Mdn = Md + (size_t)(c + 1) * envT;
         if (a1 != b2) {  // diagonal (r,c)-(r+1,c+1)
-          pair_step_fused<R, D, Dc>(false, E, X1, Muc, tptr(a, i1, b2), tptr(a, i2, a2), Mdc, nullptr, sm, red);
+          int eX = 0;
+          pair_step_fused<R, D, Dc>(false, E, X1, Muc, tptr(a, i1, b2), tptr(a, i2, a2), Mdc, nullptr, sm, red, &eX);
           const R wp = pair_step_fused<R, D, Dc>(false, X1, nullptr, Mun, tptr(a, j1, b1), tptr(a, j2, a1), Mdn,
                                                  Hb + (size_t)(c + 2) * envT2, sm, red);
-          if (ok) ev += 0.5 * g.J2 * ((double)wp / (double)W);
+          if (ok) ev += 0.5 * g.J2 * ldexp((double)wp / (double)W, eE + eX + eH[c + 2] - eH[0]);
         }
         if (b1 != a2) {  // anti-diagonal (r,c+1)-(r+1,c)
-          pair_step_fused<R, D, Dc>(false, E, X1, Muc, tptr(a, i1, a1), tptr(a, i2, b1), Mdc, nullptr, sm, red);
+          int eX = 0;
+          pair_step_fused<R, D, Dc>(false, E, X1, Muc, tptr(a, i1, a1), tptr(a, i2, b1), Mdc, nullptr, sm, red, &eX);
           const R wp = pair_step_fused<R, D, Dc>(false, X1, nullptr, Mun, tptr(a, j1, a2), tptr(a, j2, b2), Mdn,
                                                  Hb + (size_t)(c + 2) * envT2, sm, red);
-          if (ok) ev += 0.5 * g.J2 * ((double)wp / (double)W);
+          if (ok) ev += 0.5 * g.J2 * ldexp((double)wp / (double)W, eE + eX + eH[c + 2] - eH[0]);
         }
       }
       if (c < Lx - 1) {
-        pair_step_fused<R, D, Dc>(false, E, En, Muc, tptr(a, i1, a1), tptr(a, i2, a2), Mdc, nullptr, sm, red);
+        int e1 = 0;
+        pair_step_fused<R, D, Dc>(false, E, En, Muc, tptr(a, i1, a1), tptr(a, i2, a2), Mdc, nullptr, sm, red, &e1);
+        eE += e1;
         E = En;
         En = (En == E0) ? E1 : E0;
       }
@@ -697,25 +736,32 @@ __global__ void __launch_bounds__(kThreads) k_pair_tc(KArgs<float> a) {
   // B tiles of site i, spin s, direction dir (0 left, 1 right): TA at +0, TB at +kTcTile
   auto tile = [&](int dir, int i, int sp_) { return a.tcB + ((size_t)(dir * g.N + i) * 2 + sp_) * 2 * kTcTile; };
   const int npairs = Ly - 1;
+  __shared__ int eH[kMaxL + 1];   // H_c is stored scaled by 2^-eH[c]
   for (int item = blockIdx.x; item < a.n * npairs && st.ok; item += gridDim.x) {
     const int cfg = item / npairs, r = item % npairs;
     __syncthreads();
     for (int i = threadIdx.x; i < g.nwords; i += blockDim.x) sp[i] = a.S[(size_t)cfg * g.nwords + i];
     for (int e = threadIdx.x; e < envT2; e += blockDim.x) Hb[(size_t)Lx * envT2 + e] = a.triv_t2[e];
+    if (threadIdx.x == 0) eH[Lx] = 0;
     __syncthreads();
     const float* Mu = r == 0 ? a.triv_mps : a.envU + ((size_t)cfg * Ly + (r - 1)) * Lx * envT;
     const float* Md = r + 2 > Ly - 1 ? a.triv_mps : a.envL + ((size_t)cfg * Ly + (r + 2)) * Lx * envT;
+    int eacc = 0;
     for (int c = Lx - 1; c >= 0; --c) {
       const int s1 = r * Lx + c, s2 = (r + 1) * Lx + c;
+      int e = 0;
       pair_step_tc(st, true, Hb + (size_t)(c + 1) * envT2, Hb + (size_t)c * envT2, Mu + (size_t)c * envT,
                    tile(1, s1, spin_of(sp, s1)), tile(1, s2, spin_of(sp, s2)) + kTcTile, Md + (size_t)c * envT,
-                   nullptr, sm, red);
+                   nullptr, sm, red, &e);
+      eacc += e;
+      if (threadIdx.x == 0) eH[c] = eacc;
     }
     __syncthreads();
     const float W = Hb[0];
     const bool ok = W != 0.f;
     double ev = 0.0;
     const float* E = a.triv_t2;
+    int eE = 0;   // E is stored scaled by 2^-eE
     float* En = E0;
     for (int c = 0; c < Lx; ++c) {
       const int i1 = r * Lx + c, i2 = (r + 1) * Lx + c;
@@ -725,7 +771,7 @@ __global__ void __launch_bounds__(kThreads) k_pair_tc(KArgs<float> a) {
       if (a1 != a2) {
         const float wp = pair_step_tc(st, false, E, nullptr, Muc, tile(0, i1, a2), tile(0, i2, a1) + kTcTile, Mdc,
                                       Hb + (size_t)(c + 1) * envT2, sm, red);
-        if (ok) ev += 0.5 * g.J1 * ((double)wp / (double)W);
+        if (ok) ev += 0.5 * g.J1 * ldexp((double)wp / (double)W, eE + eH[c + 1] - eH[0]);
       }
       if (c < Lx - 1 && g.J2 != 0.0) {
         const int j1 = i1 + 1, j2 = i2 + 1;
@@ -733,23 +779,29 @@ __global__ void __launch_bounds__(kThreads) k_pair_tc(KArgs<float> a) {
         const float* Mun = Mu + (size_t)(c + 1) * envT;
         const float* Mdn = Md + (size_t)(c + 1) * envT;
         if (a1 != b2) {
-          pair_step_tc(st, false, E, X1, Muc, tile(0, i1, b2), tile(0, i2, a2) + kTcTile, Mdc, nullptr, sm, red);
+          int eX = 0;
+          pair_step_tc(st, false, E, X1, Muc, tile(0, i1, b2), tile(0, i2, a2) + kTcTile, Mdc, nullptr, sm, red,
+                       &eX);
           __syncthreads();
           const float wp = pair_step_tc(st, false, X1, nullptr, Mun, tile(0, j1, b1), tile(0, j2, a1) + kTcTile, Mdn,
                                         Hb + (size_t)(c + 2) * envT2, sm, red);
-          if (ok) ev += 0.5 * g.J2 * ((double)wp / (double)W);
+          if (ok) ev += 0.5 * g.J2 * ldexp((double)wp / (double)W, eE + eX + eH[c + 2] - eH[0]);
         }
         if (b1 != a2) {
-          pair_step_tc(st, false, E, X1, Muc, tile(0, i1, a1), tile(0, i2, b1) + kTcTile, Mdc, nullptr, sm, red);
+          int eX = 0;
+          pair_step_tc(st, false, E, X1, Muc, tile(0, i1, a1), tile(0, i2, b1) + kTcTile, Mdc, nullptr, sm, red,
+                       &eX);
           __syncthreads();
           const float wp = pair_step_tc(st, false, X1, nullptr, Mun, tile(0, j1, a2), tile(0, j2, b2) + kTcTile, Mdn,
                                         Hb + (size_t)(c + 2) * envT2, sm, red);
-          if (ok) ev += 0.5 * g.J2 * ((double)wp / (double)W);
+          if (ok) ev += 0.5 * g.J2 * ldexp((double)wp / (double)W, eE + eX + eH[c + 2] - eH[0]);
         }
       }
       if (c < Lx - 1) {
-        pair_step_tc(st, false, E, En, Muc, tile(0, i1, a1), tile(0, i2, a2) + kTcTile, Mdc, nullptr, sm, red);
+        int e1 = 0;
+        pair_step_tc(st, false, E, En, Muc, tile(0, i1, a1), tile(0, i2, a2) + kTcTile, Mdc, nullptr, sm, red, &e1);
         __syncthreads();
+        eE += e1;
         E = En;
         En = (En == E0) ? E1 : E0;
       }
@@ -923,6 +975,7 @@ __global__ void __launch_bounds__(kThreads) k_mc(KArgs<R> a, uint64_t* S, int ns
   R* t0 = p; p += tmp_elems(g);
   R* t1 = p;
   for (int i = threadIdx.x; i <= Lx; i += blockDim.x) ones[i] = 1;
+  __shared__ int eH[kMaxL + 1];   // H_c is stored scaled by 2^-eH[c]
   const int nh = Ly * (Lx - 1);
   for (int chain = blockIdx.x; chain < a.n; chain += gridDim.x) {
     __syncthreads();
@@ -951,7 +1004,9 @@ __global__ void __launch_bounds__(kThreads) k_mc(KArgs<R> a, uint64_t* S, int ns
           const size_t tsz = pass == 0 ? envT : envT2;
           const R* triv = pass == 0 ? a.triv_t1 : a.triv_t2;
           for (size_t e = threadIdx.x; e < tsz; e += blockDim.x) Hb[(size_t)Lx * tsz + e] = triv[e];
+          if (threadIdx.x == 0) eH[Lx] = 0;
           __syncthreads();
+          int eacc = 0;
           for (int c = Lx - 1; c >= 0; --c) {
             const int i1 = r * Lx + c;
             if (pass == 0)
@@ -961,6 +1016,8 @@ __global__ void __launch_bounds__(kThreads) k_mc(KArgs<R> a, uint64_t* S, int ns
               run_op<R>(OP_COL2_RIGHT, D, Dc, Hb + (size_t)(c + 1) * tsz, Mu + (size_t)c * envT,
                         tptr(a, i1, spin_of(sp, i1)), tptr(a, i1 + Lx, spin_of(sp, i1 + Lx)),
                         Md + (size_t)c * envT, Hb + (size_t)c * tsz, t0, t1, gsm, gism);
+            eacc += normalize_pow2(Hb + (size_t)c * tsz, (int)tsz, red);
+            if (threadIdx.x == 0) eH[c] = eacc;
           }
           const R* E = triv;
           int e = 3;   // index in Q of the buffer E lives in (none yet)
@@ -996,7 +1053,9 @@ __global__ void __launch_bounds__(kThreads) k_mc(KArgs<R> a, uint64_t* S, int ns
               if (w == R(0)) {
                 take = true;
               } else {
-                const double ratio = (double)wp / (double)w;
+                // the E scale is common to w and wp; the H scales differ by a column in a horizontal exchange
+                const double ratio =
+                    pass == 0 ? ldexp((double)wp / (double)w, eH[c + 2] - eH[c + 1]) : (double)wp / (double)w;
                 take = u < ratio * ratio;
               }
               if (take) {
@@ -1019,6 +1078,8 @@ __global__ void __launch_bounds__(kThreads) k_mc(KArgs<R> a, uint64_t* S, int ns
             }
             e = chosen;
             E = Q[e];
+            // E's own scale cancels in every ratio: renormalise without tracking
+            normalize_pow2(Q[e], (int)tsz, red);
           }
           if (pass == 0 ? (r < Ly - 1) : true) {
             const int* bdin = r == 0 ? ones : a.bd + ((size_t)0 * Ly + (r - 1)) * (Lx + 1);

@@ -8,6 +8,7 @@
 namespace peps {
 
 constexpr int kMaxWords = 64;        // up to 4096 sites
+constexpr int kMaxL = 64;            // Lx, Ly <= 64
 constexpr int kMaxDc = 32;           // K <= 32 in the truncation
 constexpr int kMaxDcD = 256;         // Dc * D <= 256
 

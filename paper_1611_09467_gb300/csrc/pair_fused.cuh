@@ -72,12 +72,13 @@ __device__ __forceinline__ void smem_gemm_km(const R* __restrict__ A, const R* _
 // right == true: right step (H_{c+1} -> H_c).  Mu, Md: padded [Dc][D][Dc]
 // boundary-MPS tensors of column c; T1, T2: padded [l][r][u][d] site
 // tensors of rows r, r+1 at the chosen spins.  If Hdot is null the result is
-// written to Eout; otherwise <result, Hdot> is returned (all threads) and
+// written to Eout scaled by 2^-e (pow2_exponent of its largest entry) and e
+// is stored in *e_out; otherwise <result, Hdot> is returned (all threads) and
 // nothing is written.  Ends with a barrier.
 template <typename R, int D, int Dc>
-__device__ R pair_step_fused(bool right, const R* __restrict__ Ein, R* __restrict__ Eout, const R* __restrict__ Mu,
+__device__ R pair_step_fused(bool right, const R* Ein, R* __restrict__ Eout, const R* __restrict__ Mu,
                              const R* __restrict__ T1, const R* __restrict__ T2, const R* __restrict__ Md,
-                             const R* __restrict__ Hdot, R* sm, R* red) {
+                             const R* Hdot, R* sm, R* red, int* e_out = nullptr) {
   using S = PairSmem<D, Dc>;
   constexpr int DD = S::DD, D3 = DD * D;
   R* P1 = sm;
@@ -151,12 +152,23 @@ __device__ R pair_step_fused(bool right, const R* __restrict__ Ein, R* __restric
   }
   R dot = R(0);
   if (Hdot == nullptr) {
+    R mx = R(0);
 #pragma unroll
     for (int q = 0; q < S::RPT; ++q) {
       const int row = q * kThreads + tid;
       if (S::ROWS % kThreads == 0 || row < S::ROWS)
 #pragma unroll
-        for (int x = 0; x < Dc; ++x) Eout[x * S::ROWS + row] = acc[q][x];
+        for (int x = 0; x < Dc; ++x) mx = fmax(mx, fabs(acc[q][x]));
+    }
+    const int e = pow2_exponent(block_max(mx, red));
+    const R sc = pow2<R>(-e);
+    if (e_out) *e_out = e;
+#pragma unroll
+    for (int q = 0; q < S::RPT; ++q) {
+      const int row = q * kThreads + tid;
+      if (S::ROWS % kThreads == 0 || row < S::ROWS)
+#pragma unroll
+        for (int x = 0; x < Dc; ++x) Eout[x * S::ROWS + row] = acc[q][x] * sc;
     }
     __syncthreads();
   } else {

@@ -159,11 +159,12 @@ __device__ __forceinline__ void st4(float* p, float a, float b, float c, float d
 
 // One two-row transfer step, D = 8, Dc = 16, TF32 tensor cores.  Arguments
 // as pair_step_fused, plus the pre-arranged B tiles of T1 (TA) and T2 (TB).
-// Returns <result, Hdot> when Hdot is given.
-__device__ float pair_step_tc(PairTc& st, bool right, const float* __restrict__ Ein, float* __restrict__ Eout,
+// Returns <result, Hdot> when Hdot is given; otherwise writes the result
+// scaled by 2^-e to Eout and stores e in *e_out, as pair_step_fused.
+__device__ float pair_step_tc(PairTc& st, bool right, const float* Ein, float* __restrict__ Eout,
                               const float* __restrict__ Mu, const float* __restrict__ TA1,
                               const float* __restrict__ TB2, const float* __restrict__ Md,
-                              const float* __restrict__ Hdot, float* sm, float* red) {
+                              const float* Hdot, float* sm, float* red, int* e_out = nullptr) {
   constexpr int D = 8, Dc = 16;
   using S = PairTcSmem;
   float* A1 = sm;
@@ -297,14 +298,31 @@ __device__ float pair_step_tc(PairTc& st, bool right, const float* __restrict__ 
   }
   // ---- result: tile t rows t*128 + row, 16 columns x'o
   float dot = 0.f;
-  for (int t = half; t < 8; t += 2) {
-    float v[16];
-    tc::ld16(st.tmem + lane_base + tc::kColE + t * 16, v);
-    const int m = t * 128 + row;
-    if (Hdot == nullptr) {
+  if (Hdot == nullptr) {
+    float mx = 0.f;
+    for (int t = half; t < 8; t += 2) {
+      float v[16];
+      tc::ld16(st.tmem + lane_base + tc::kColE + t * 16, v);
 #pragma unroll
-      for (int x = 0; x < Dc; ++x) Eout[x * 1024 + m] = v[x];
-    } else {
+      for (int x = 0; x < Dc; ++x) mx = fmaxf(mx, fabsf(v[x]));
+    }
+    tc::tc_fence_before();
+    const int e = pow2_exponent(block_max(mx, red));
+    tc::tc_fence_after();
+    const float sc = pow2<float>(-e);
+    if (e_out) *e_out = e;
+    for (int t = half; t < 8; t += 2) {
+      float v[16];
+      tc::ld16(st.tmem + lane_base + tc::kColE + t * 16, v);
+      const int m = t * 128 + row;
+#pragma unroll
+      for (int x = 0; x < Dc; ++x) Eout[x * 1024 + m] = v[x] * sc;
+    }
+  } else {
+    for (int t = half; t < 8; t += 2) {
+      float v[16];
+      tc::ld16(st.tmem + lane_base + tc::kColE + t * 16, v);
+      const int m = t * 128 + row;
 #pragma unroll
       for (int x = 0; x < Dc; ++x) dot = fmaf(v[x], Hdot[x * 1024 + m], dot);
     }

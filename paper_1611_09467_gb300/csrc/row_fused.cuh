@@ -49,12 +49,14 @@ struct RowSmem {
 // One fused single-row transfer step.  right == false: F_{c-1} -> F_c;
 // right == true: G_{c+1} -> G_c.  Mu, Md: padded [Dc][D][Dc] boundary-MPS
 // tensors of column c; T: padded [l][r][u][d] site tensor at the chosen spin.
-// If Gdot is null the result is written to Fout; otherwise <result, Gdot> is
-// returned (all threads) and nothing is written.  Ends with a barrier.
+// If Gdot is null the result is written to Fout scaled by 2^-e
+// (pow2_exponent of its largest entry) and e is stored in *e_out; otherwise
+// <result, Gdot> is returned (all threads) and nothing is written.  Ends with
+// a barrier.
 template <typename R, int D, int Dc>
-__device__ R row_step_fused(bool right, const R* __restrict__ Fin, R* __restrict__ Fout, const R* __restrict__ Mu,
-                            const R* __restrict__ T, const R* __restrict__ Md, const R* __restrict__ Gdot, R* sm,
-                            R* red) {
+__device__ R row_step_fused(bool right, const R* Fin, R* __restrict__ Fout, const R* __restrict__ Mu,
+                            const R* __restrict__ T, const R* __restrict__ Md, const R* Gdot, R* sm,
+                            R* red, int* e_out = nullptr) {
   using S = RowSmem<D, Dc>;
   constexpr int DD = S::DD, D3 = S::D3, XY = Dc * D;
   R* Mus = sm;
@@ -113,16 +115,28 @@ __device__ R row_step_fused(bool right, const R* __restrict__ Fin, R* __restrict
     }
   }
   R dot = R(0);
+  if (Gdot == nullptr) {
+    R mx = R(0);
 #pragma unroll
-  for (int q = 0; q < S::OPT; ++q) {
-    const int o = q * kThreads + tid;
-    if (S::OUT % kThreads == 0 || o < S::OUT) {
-      if (Gdot == nullptr) Fout[o] = acc[q];
-      else dot = fma(acc[q], Gdot[o], dot);
+    for (int q = 0; q < S::OPT; ++q)
+      if (S::OUT % kThreads == 0 || q * kThreads + tid < S::OUT) mx = fmax(mx, fabs(acc[q]));
+    const int e = pow2_exponent(block_max(mx, red));
+    const R sc = pow2<R>(-e);
+    if (e_out) *e_out = e;
+#pragma unroll
+    for (int q = 0; q < S::OPT; ++q) {
+      const int o = q * kThreads + tid;
+      if (S::OUT % kThreads == 0 || o < S::OUT) Fout[o] = acc[q] * sc;
     }
+    __syncthreads();
+  } else {
+#pragma unroll
+    for (int q = 0; q < S::OPT; ++q) {
+      const int o = q * kThreads + tid;
+      if (S::OUT % kThreads == 0 || o < S::OUT) dot = fma(acc[q], Gdot[o], dot);
+    }
+    dot = block_sum(dot, red);
   }
-  if (Gdot != nullptr) dot = block_sum(dot, red);
-  else __syncthreads();
   return dot;
 }
 
@@ -130,8 +144,8 @@ __device__ R row_step_fused(bool right, const R* __restrict__ Fin, R* __restrict
 // F_{c-1} ([a'][a][l]), Mu, Md (padded [Dc][D][Dc]) and G_{c+1} ([b'][b][r]).
 // Ends with a barrier.
 template <typename R, int D, int Dc>
-__device__ void site_env_fused(const R* __restrict__ F, const R* __restrict__ Mu, const R* __restrict__ Md,
-                               const R* __restrict__ G, R scale, R* __restrict__ Bout, R* sm) {
+__device__ void site_env_fused(const R* F, const R* __restrict__ Mu, const R* __restrict__ Md,
+                               const R* G, R scale, R* __restrict__ Bout, R* sm) {
   using S = RowSmem<D, Dc>;
   constexpr int DD = S::DD, D3 = S::D3, XY = Dc * D, TM = S::TM;
   R* Mus = sm;                 // Mu as stored: [a][(u,b)]
