@@ -884,6 +884,9 @@ __device__ void cta_topk_left(const R* X, int m, int n, int K, TruncWork<R>& w, 
         }
       }
     }
+    // the last column's diagonal entry (w.t[2Q-2], written by thread 0) is
+    // read by another warp in the bisection set-up below
+    __syncthreads();
   }   // !tiled
   PEPS_PHASE(1);
   // ---------------- Sturm bisection for the K largest singular values

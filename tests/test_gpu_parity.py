@@ -58,6 +58,8 @@ CASES_FP64 = [
     (5, 4, 3, 9, 0.0, 8, False, 79),           # J2 = 0, exact
     (2, 6, 2, 2, 0.5, 10, False, 80),          # two rows only, truncated
     (6, 5, 4, 8, 0.5, 6, True, 81),            # fused two-row step (D=4, Dc=8), truncated
+    (4, 4, 8, 16, 0.5, 4, False, 82),          # D=8: cut blocks of up to 128 x 128, fused row step
+    (5, 6, 6, 12, 0.5, 4, True, 83),           # D=6: cut blocks of up to 72 rows
 ]
 
 
@@ -284,4 +286,31 @@ def test_mc_sweep_matches_oracle(Ly, Lx, D, Dc):
             mism += 1
         assert got[k].sum() == Ly * Lx // 2
     assert mism == 0, mism
+    p.close()
+
+
+def test_fp64_batched_repeatable():
+    """Batched FP64 sweeps at 6x6 D=8 Dc=16 (cut blocks of up to 128 rows,
+    many CTAs at once) give bit-identical ln|psi| on every run, equal to the
+    one-configuration-per-call results.  A missing barrier shows up exactly
+    this way: only under many concurrent CTAs, and only now and then, as a
+    changed result on a badly conditioned lattice."""
+    L, D, Dc = 6, 8, 16
+    A = inputs.make_tensors(L, L, D, 84)
+    spins = inputs.random_sz0(96, L * L, 84)
+    p = make(A, L, L, D, Dc, 0.5, "fp64")
+    S = packed(spins)
+    runs = []
+    for _ in range(3):
+        r = p.evaluate(S, logabs=True, eloc=False, O=False)
+        torch.cuda.synchronize()
+        runs.append(r["logabs"].cpu().numpy().copy())
+    for k in (1, 2):
+        assert np.array_equal(runs[k], runs[0]), np.flatnonzero(runs[k] != runs[0])
+    single = []
+    for k in range(8):
+        r = p.evaluate(S[k:k + 1], logabs=True, eloc=False, O=False)
+        torch.cuda.synchronize()
+        single.append(r["logabs"].cpu().numpy()[0])
+    assert np.array_equal(np.array(single), runs[0][:8])
     p.close()
