@@ -113,6 +113,32 @@ def make_tensors(Ly: int, Lx: int, D: int, seed: int, d: int = 2,
     return A / norms[:, None, None, None, None, None]
 
 
+def near_product_tensors(Ly: int, Lx: int, D: int, seed: int, d: int = 2, eta: float = 1.0) -> np.ndarray:
+    """Padded site tensors [N][d][D][D][D][D] (float64) near a product state.
+
+    A_i[s] = phi_i(s) on the all-zero bond index plus i.i.d. N(0, 1) noise
+    scaled so that its expected Frobenius norm is ``eta`` times that of the
+    product part; phi_i = (cos t_i, sin t_i) with t_i keyed uniform in
+    [pi/8, 3pi/8].  Each site is then scaled to unit Frobenius norm over its
+    true dimensions.  Such tensors have decaying bond spectra, as optimised
+    ground-state PEPS do, so truncation to Dc is well conditioned; i.i.d.
+    tensors at D = 8, Dc = 16 are not (FP32-sized perturbations move the FP64
+    ln|psi| by O(1)).  Entries are keyed by (site, s, flat index).
+    """
+    N = Ly * Lx
+    site = np.arange(N)[:, None, None]
+    s = np.arange(d)[None, :, None]
+    flat = np.arange(D ** 4)[None, None, :]
+    eps = eta / np.sqrt(d * D ** 4)
+    A = eps * keyed_normal(seed, 0, site, s, flat).reshape(N, d, D, D, D, D)
+    t = np.pi / 8 + np.pi / 4 * keyed_uniform(seed, 2, np.arange(N))
+    A[:, 0, 0, 0, 0, 0] += np.cos(t)
+    A[:, 1, 0, 0, 0, 0] += np.sin(t)
+    A = A * edge_mask(Ly, Lx, D)
+    norms = np.sqrt((A.reshape(N, -1) ** 2).sum(axis=1))
+    return A / norms[:, None, None, None, None, None]
+
+
 def n_words(N: int) -> int:
     return (N + 63) // 64
 
@@ -169,6 +195,9 @@ WORKLOADS = {
                           sampling="metropolis10"),
     "16x16_D10_Dc20": dict(L=16, D=10, Dc=20, J2=0.5, n=16384, bias=False, cfg=4,
                            sampling="metropolis10"),
+    # the same shapes with near-product tensors: for accuracy checks at full size
+    "16x16_D8_Dc16_np": dict(L=16, D=8, Dc=16, J2=0.5, n=16384, bias=False, cfg=5,
+                             sampling="uniform", tensors="near_product"),
 }
 
 
@@ -176,6 +205,9 @@ def workload_inputs(name: str, n: int | None = None, first: int = 0):
     """(A, spins) for a named workload; ``n`` overrides the batch size."""
     w = WORKLOADS[name]
     seed = SEED_BASE + w["cfg"]
-    A = make_tensors(w["L"], w["L"], w["D"], seed, bias_zero_index=w["bias"])
+    if w.get("tensors") == "near_product":
+        A = near_product_tensors(w["L"], w["L"], w["D"], seed)
+    else:
+        A = make_tensors(w["L"], w["L"], w["D"], seed, bias_zero_index=w["bias"])
     spins = random_sz0(w["n"] if n is None else n, w["L"] * w["L"], seed, first)
     return A, spins
