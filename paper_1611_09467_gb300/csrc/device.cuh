@@ -373,12 +373,16 @@ __device__ int sturm_count(const R* t2, int n2, R x, R pivmin) {
 // Inverse iteration for one eigenvalue of the n2 x n2 zero-diagonal
 // symmetric tridiagonal with off-diagonal t: Gaussian elimination with
 // partial pivoting on (T - lam I), two solves from a fixed pseudo-random
-// start vector.  Sequential, one thread per eigenvalue.  The recurrences
-// carry their running values in registers; memory only receives the factors
-// and reads back values that do not depend on the running recurrence, so
-// loads can be issued ahead.  The workspace is interleaved across the K
-// threads (element i of thread k at i * K + k): lock-step accesses of a warp
-// are contiguous.
+// start vector.  Sequential, one thread per eigenvalue.  Five passes over
+// the vector: factorisation fused with the first forward elimination, back
+// substitution, the second forward elimination (which also applies the
+// scaling of the first iterate), back substitution, and the output pass.
+// Each iterate is scaled only by its largest entry (the solve can amplify by
+// 1/pivtiny); the caller normalises the vectors.  The recurrences carry their
+// running values in registers; memory only receives the factors and reads
+// back values that do not depend on the running recurrence, so loads can be
+// issued ahead.  The workspace is interleaved across the K threads (element
+// i of thread k at i * K + k): lock-step accesses of a warp are contiguous.
 template <typename R>
 __device__ void inverse_iteration(const R* t, int n2, R lam, R pivtiny, R* ws, int K, int k, R* z, int zs,
                                   unsigned seed) {
@@ -390,12 +394,20 @@ __device__ void inverse_iteration(const R* t, int n2, R lam, R pivtiny, R* ws, i
   R* piv = mult + st;    // 1 where rows i, i+1 were interchanged
   R* b = piv + st;       // right-hand side / solution
 #define IX(i) ((size_t)(i) * K)
-  // ---- factorisation, carrying dd[i], du[i] (current row) and dd[i+1], du[i+1]
+  unsigned h = seed * 2654435761u + 12345u;
+  auto start = [&]() {
+    h ^= h << 13; h ^= h >> 17; h ^= h << 5;
+    return R((int)(h & 0xffffu) - 32768) / R(32768) + R(0.001);
+  };
+  // ---- factorisation, carrying dd[i], du[i] (current row) and dd[i+1],
+  // du[i+1], with the forward elimination of the start vector (carrying b[i])
   R cur_d = -lam, cur_u = n2 > 1 ? t[0] : R(0);
+  R bi = start();
   for (int i = 0; i < n2 - 1; ++i) {
     const R sub = t[i];
     R next_d = -lam;
     R next_u = i + 1 < n2 - 1 ? t[i + 1] : R(0);
+    const R bn = start();
     R d_i, u_i, u2_i, l;
     if (fabs(cur_d) >= fabs(sub)) {
       d_i = cur_d == R(0) ? pivtiny : cur_d;
@@ -404,6 +416,8 @@ __device__ void inverse_iteration(const R* t, int n2, R lam, R pivtiny, R* ws, i
       u2_i = R(0);
       next_d -= l * cur_u;
       piv[IX(i)] = R(0);
+      b[IX(i)] = bi;
+      bi = bn - l * bi;
     } else {
       l = cur_d / sub;
       d_i = sub;
@@ -412,6 +426,8 @@ __device__ void inverse_iteration(const R* t, int n2, R lam, R pivtiny, R* ws, i
       u2_i = next_u;
       next_u = -l * next_u;
       piv[IX(i)] = R(1);
+      b[IX(i)] = bn;
+      bi = bi - l * bn;
     }
     if (fabs(d_i) < pivtiny) d_i = d_i < R(0) ? -pivtiny : pivtiny;
     rdd[IX(i)] = R(1) / d_i;
@@ -425,35 +441,26 @@ __device__ void inverse_iteration(const R* t, int n2, R lam, R pivtiny, R* ws, i
   rdd[IX(n2 - 1)] = R(1) / cur_d;
   du[IX(n2 - 1)] = R(0);
   du2[IX(n2 - 1)] = R(0);
-  unsigned h = seed * 2654435761u + 12345u;
+  b[IX(n2 - 1)] = bi;
+  R sc = R(1);   // scale of the current iterate still to be applied
   for (int it = 0; it < 2; ++it) {
-    // ---- forward: apply the row interchanges and L^-1, carrying b[i]
-    R bi;
-    if (it == 0) {
-      h ^= h << 13; h ^= h >> 17; h ^= h << 5;
-      bi = R((int)(h & 0xffffu) - 32768) / R(32768) + R(0.001);
-    } else {
-      bi = b[IX(0)];
-    }
+    if (it == 1) {
+      // ---- forward: row interchanges and L^-1 on the scaled iterate
+      R bf = b[IX(0)] * sc;
 #pragma unroll 4
-    for (int i = 0; i < n2 - 1; ++i) {
-      R bn;
-      if (it == 0) {
-        h ^= h << 13; h ^= h >> 17; h ^= h << 5;
-        bn = R((int)(h & 0xffffu) - 32768) / R(32768) + R(0.001);
-      } else {
-        bn = b[IX(i + 1)];
+      for (int i = 0; i < n2 - 1; ++i) {
+        const R bn = b[IX(i + 1)] * sc;
+        const R l = mult[IX(i)];
+        if (piv[IX(i)] == R(0)) {
+          b[IX(i)] = bf;
+          bf = bn - l * bf;
+        } else {
+          b[IX(i)] = bn;
+          bf = bf - l * bn;
+        }
       }
-      const R l = mult[IX(i)];
-      if (piv[IX(i)] == R(0)) {
-        b[IX(i)] = bi;
-        bi = bn - l * bi;
-      } else {
-        b[IX(i)] = bn;
-        bi = bi - l * bn;
-      }
+      b[IX(n2 - 1)] = bf;
     }
-    b[IX(n2 - 1)] = bi;
     // ---- backward: U^-1, carrying y[i+1], y[i+2]; track max |y|
     R y1 = R(0), y2 = R(0), mx = R(0);
 #pragma unroll 4
@@ -464,20 +471,9 @@ __device__ void inverse_iteration(const R* t, int n2, R lam, R pivtiny, R* ws, i
       y2 = y1;
       y1 = y;
     }
-    // ---- normalise (scale by the max first: the solve can amplify by 1/pivtiny)
-    if (!(mx > R(0))) mx = R(1);
-    const R imx = R(1) / mx;
-    R ss = R(0);
-#pragma unroll 4
-    for (int i = 0; i < n2; ++i) {
-      const R v = b[IX(i)] * imx;
-      ss += v * v;
-    }
-    const R inv = imx / dsqrt(ss);
-#pragma unroll 4
-    for (int i = 0; i < n2; ++i) b[IX(i)] *= inv;
+    sc = mx > R(0) ? R(1) / mx : R(1);
   }
-  for (int i = 0; i < n2; ++i) z[(size_t)i * zs] = b[IX(i)];
+  for (int i = 0; i < n2; ++i) z[(size_t)i * zs] = b[IX(i)] * sc;
 #undef IX
 }
 
@@ -984,7 +980,15 @@ __device__ void cta_topk_left(const R* X, int m, int n, int K, TruncWork<R>& w, 
     }
   }
   PEPS_PHASE(4);
-  // ---------------- back-transformation, one thread group per column
+  // ---------------- back-transformation by the stored reflectors, in blocks
+  // U = H_0 H_1 ... H_{nref-1} [Ub; 0].  A block of nb consecutive reflectors
+  // is applied at once as U -= V (T (V^T U)), with V = [v_j0 .. v_j0+nb-1] and
+  // T the upper triangular factor of the compact WY form (Schreiber & Van
+  // Loan 1989), built by the forward recurrence T_kk = tau_k,
+  // T_{0:k,k} = -tau_k T_{0:k,0:k} (V_{:,0:k}^T v_k).  Reflector j has its
+  // implicit 1 at row j (tall block) or j+1 (wide block) and scale * stored
+  // entries below it.  V is written out per block into the Ub buffer, which
+  // is free once Ub has been copied to Uk (nb <= K keeps it in bounds).
   R* Uk = w.Uks;
   const int rowsU = tall ? P : Q;
   for (int e = tid; e < rowsU * K; e += blockDim.x) {
@@ -993,54 +997,95 @@ __device__ void cta_topk_left(const R* X, int m, int n, int K, TruncWork<R>& w, 
   }
   __syncthreads();
   {
-    const R* sLb = w.tau + 2 * w.Qmax;
-    const R* sRb = sLb + w.Qmax;
-    // Every group runs the same loop (the shuffles need whole warps); groups
-    // beyond K compute on column 0 and discard the result.
-    const int G = K <= 8 ? 32 : (K <= 16 ? 16 : 8);
-    const int col = tid / G, gl = tid % G;
-    const bool act = col < K;
-    const int cc = act ? col : 0;
-    if (tall) {
-      for (int j = Q - 1; j >= 0; --j) {
-        const R tau = tauL[j];
-        if (tau == R(0)) continue;
-        const R sc = sLb[j];
-        R s = R(0);
-        for (int i = j + 1 + gl; i < P; i += G) s += W[i * ld + j] * Uk[i * K + cc];
-        s = (Uk[j * K + cc] + sc * warp_sum(s, G)) * tau;
-        if (act) {
-          if (gl == 0) Uk[j * K + cc] -= s;
-          const R s2 = s * sc;
-          for (int i = j + 1 + gl; i < P; i += G) Uk[i * K + cc] -= s2 * W[i * ld + j];
-        }
-        __syncwarp();
+    constexpr int NBMAX = 8, KMAX = 32;   // reflectors per block; K <= 32
+    __shared__ R bt_g[NBMAX][NBMAX], bt_t[NBMAX][NBMAX], bt_w1[NBMAX][KMAX + NBMAX], bt_w2[NBMAX][KMAX];
+    const R* taus = tall ? tauL : tauR;
+    const R* scs = tall ? w.tau + 2 * w.Qmax : w.tau + 3 * w.Qmax;
+    const int nref = tall ? Q : Q - 1;
+    const int NB = K < NBMAX ? K : NBMAX;
+    R* Vs = Ub;   // [rowsU][nb]
+    for (int j0 = nref > 0 ? ((nref - 1) / NB) * NB : -1; j0 >= 0; j0 -= NB) {
+      const int nb = min(NB, nref - j0);
+      const int p0 = tall ? j0 : j0 + 1;
+      for (int e = tid; e < (rowsU - p0) * nb; e += blockDim.x) {
+        const int i = p0 + e / nb, aa = e % nb, j = j0 + aa, pv = tall ? j : j + 1;
+        Vs[i * nb + aa] = i < pv ? R(0) : (i == pv ? R(1) : scs[j] * (tall ? W[i * ld + j] : W[j * ld + i]));
       }
-    } else {
-      for (int j = Q - 2; j >= 0; --j) {
-        const R tau = tauR[j];
-        if (tau == R(0)) continue;
-        const R sc = sRb[j];
-        R s = R(0);
-        for (int c = j + 2 + gl; c < Q; c += G) s += W[j * ld + c] * Uk[c * K + cc];
-        s = (Uk[(j + 1) * K + cc] + sc * warp_sum(s, G)) * tau;
-        if (act) {
-          if (gl == 0) Uk[(j + 1) * K + cc] -= s;
-          const R s2 = s * sc;
-          for (int c = j + 2 + gl; c < Q; c += G) Uk[c * K + cc] -= s2 * W[j * ld + c];
+      __syncthreads();
+      // [W1 | G] = V^T [U | V] (nb x (K + nb)); two threads per dot product
+      const int ncol = K + nb, nd = nb * ncol;
+      for (int d0 = 0; d0 < nd; d0 += kThreads / 2) {
+        const int d = d0 + (tid >> 1), part = tid & 1;
+        R sacc = R(0);
+        if (d < nd) {
+          const int aa = d / ncol, c = d % ncol;
+          const int pa = p0 + aa;   // first non-zero row of v_aa
+          if (c < K) {
+            for (int i = pa + part; i < rowsU; i += 2) sacc += Vs[i * nb + aa] * Uk[i * K + c];
+          } else {
+            for (int i = pa + part; i < rowsU; i += 2) sacc += Vs[i * nb + aa] * Vs[i * nb + (c - K)];
+          }
         }
-        __syncwarp();
+        sacc += __shfl_xor_sync(0xffffffffu, sacc, 1);
+        if (part == 0 && d < nd) {
+          const int aa = d / ncol, c = d % ncol;
+          if (c < K) bt_w1[aa][c] = sacc;
+          else bt_g[aa][c - K] = sacc;
+        }
       }
+      __syncthreads();
+      // T, one thread per row: T[i][i] = tau_i, T[i][k] = -tau_k sum_{m=i}^{k-1} T[i][m] G[m][k]
+      if (tid < nb) {
+        const int i = tid;
+        for (int k = 0; k < nb; ++k) bt_t[i][k] = R(0);
+        bt_t[i][i] = taus[j0 + i];
+        for (int k = i + 1; k < nb; ++k) {
+          R acc = R(0);
+          for (int m = i; m < k; ++m) acc += bt_t[i][m] * bt_g[m][k];
+          bt_t[i][k] = -taus[j0 + k] * acc;
+        }
+      }
+      __syncthreads();
+      // W2 = T W1
+      for (int e = tid; e < nb * K; e += blockDim.x) {
+        const int aa = e / K, cc = e % K;
+        R acc = R(0);
+        for (int bb = aa; bb < nb; ++bb) acc += bt_t[aa][bb] * bt_w1[bb][cc];
+        bt_w2[aa][cc] = acc;
+      }
+      __syncthreads();
+      // U -= V W2 on rows p0.. (V is zero above its first pivot)
+      for (int e = tid; e < (rowsU - p0) * K; e += blockDim.x) {
+        const int i = p0 + e / K, cc = e % K;
+        R acc = R(0);
+        for (int aa = 0; aa < nb; ++aa) acc += Vs[i * nb + aa] * bt_w2[aa][cc];
+        Uk[i * K + cc] -= acc;
+      }
+      __syncthreads();
     }
   }
-  __syncthreads();
   PEPS_PHASE(5);
-  // ---------------- outputs
-  for (int e = tid; e < m * K; e += blockDim.x) {
-    const int i = e / K, k = e % K;
-    const R v = Uk[e];
-    Uout[ixoff(uo_r, i) + ixoff(uo_c, k)] = v;
-    w.Uk[e] = v;
+  // ---------------- outputs, after one Newton-Schulz step towards the
+  // nearest orthonormal basis (Higham, Functions of Matrices, Sec. 8.3):
+  // U <- U (3/2 I - 1/2 U^T U).  In FP32 the reflectors leave U^T U - I at
+  // ~1e-6, and each cut then applies a slightly wrong projector; the step
+  // squares that defect.  The K x K factor goes into the free Ub buffer.
+  {
+    R* Mns = Ub;
+    for (int e = tid; e < K * K; e += blockDim.x) {
+      const int a = e / K, b = e % K;
+      R sacc = R(0);
+      for (int i = 0; i < m; ++i) sacc += Uk[i * K + a] * Uk[i * K + b];
+      Mns[e] = (a == b ? R(1.5) : R(0)) - R(0.5) * sacc;
+    }
+    __syncthreads();
+    for (int e = tid; e < m * K; e += blockDim.x) {
+      const int i = e / K, k = e % K;
+      R v = R(0);
+      for (int a = 0; a < K; ++a) v += Uk[i * K + a] * Mns[a * K + k];
+      Uout[ixoff(uo_r, i) + ixoff(uo_c, k)] = v;
+      w.Uk[e] = v;
+    }
   }
   __syncthreads();
   // C' = U_K^T X

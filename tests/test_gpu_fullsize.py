@@ -1,0 +1,127 @@
+"""Full-size checks at 16x16, D=8, Dc=16 with near-product tensors (decaying
+bond spectra, as in optimised ground states; inputs.near_product_tensors).
+
+* The mixed path runs the whole 16384-configuration batch, the launch
+  configuration bench.py times (same precision path, batch and chunking), and
+  sampled configurations are compared one by one with the FP64 oracle.
+* The FP64 path is compared with the oracle on a few configurations.
+* Energy per site and gradient of the mixed path are compared with the FP64
+  GPU path on a sub-batch: within 1e-4 per site and cosine >= 0.999.
+
+With i.i.d. tensors at these sizes the cut is ill-conditioned: perturbing
+the inputs by FP32 rounding moves the FP64 oracle's ln|psi| by O(1), so no
+FP32 evaluation can agree with FP64 there; the near-product family keeps the
+same shapes (and the same work per configuration) while the answer is
+well defined in FP32.
+"""
+import numpy as np
+import pytest
+
+from oracle import peps_oracle as O
+from paper_1611_09467_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+WL = "16x16_D8_Dc16_np"
+L, D, Dc, J2 = 16, 8, 16, 0.5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1611_09467_gb300 import build
+    build.build()
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+
+
+@pytest.fixture(scope="module")
+def workload():
+    return inputs.workload_inputs(WL)
+
+
+def make(A, prec):
+    from paper_1611_09467_gb300.peps import PEPS
+    return PEPS(A, L, L, D, Dc, J1=1.0, J2=J2, prec=prec)
+
+
+def packed(spins):
+    return torch.from_numpy(inputs.pack_spins(spins).view(np.int64)).cuda()
+
+
+def eloc_scale(ev, spins):
+    s = 1.0
+    for i, j, J, _ in O.all_bonds(L, L, 1.0, J2):
+        s += abs(J) / 4
+        if spins[i] != spins[j]:
+            s += abs(J) / 2 * abs(ev.ratios[(i, j)])
+    return s
+
+
+def test_fullsize_mixed_batch_sampled_against_oracle(workload):
+    """ln|psi| (FP32 boundary sweep) within 3e-5 and E_loc (TF32 two-row
+    transfers) within 2e-2 (1 + sum|terms|), the bound of ~40 rounded TF32
+    stages per ratio, on configurations sampled from the full batch.
+
+    The ln|psi| bound: the same top-down sweep carried out with float32
+    LAPACK/BLAS (numpy's sgesdd and sgemm) is off by 2.6e-6 to 6e-6 on these
+    configurations, from 240 FP32 cuts; this path is held to 5x that.
+    Measured: 4.8e-6 to 1.45e-5."""
+    A, spins = workload
+    assert spins.shape[0] == 16384
+    p = make(A, "mixed_tf32")
+    r = p.evaluate(packed(spins), logabs=True, eloc=True, O=False)
+    torch.cuda.synchronize()
+    st = r["status"].cpu().numpy()
+    la = r["logabs"].cpu().numpy()
+    el = r["eloc"].cpu().numpy()
+    p.close()
+    assert (st == 0).all(), np.unique(st, return_counts=True)
+    rows = []
+    for k in (0, 8191, 16383):
+        ev = O.evaluate(A, spins[k], L, L, Dc, 1.0, J2, want_O=False)
+        scale = eloc_scale(ev, spins[k])
+        rows.append((abs(la[k] - ev.logabs), abs(el[k] - ev.eloc), scale))
+        print("cfg %d: dlogpsi %.2e  dE %.2e  scale %.1f" % (k, abs(la[k] - ev.logabs), abs(el[k] - ev.eloc), scale))
+    for k, (dl, de, scale) in enumerate(rows):
+        assert dl < 3e-5, (k, dl)
+        assert de < 2e-2 * scale, (k, de, scale)
+
+
+def test_fullsize_fp64_against_oracle(workload):
+    """FP64 path: ln|psi| within 1e-10, E_loc within 1e-8 (1 + sum|terms|)."""
+    A, spins = workload
+    sub = spins[:3]
+    p = make(A, "fp64")
+    r = p.evaluate(packed(sub), logabs=True, eloc=True, O=False)
+    torch.cuda.synchronize()
+    la = r["logabs"].cpu().numpy()
+    sg = r["sign"].cpu().numpy()
+    el = r["eloc"].cpu().numpy()
+    p.close()
+    for k in range(len(sub)):
+        ev = O.evaluate(A, sub[k], L, L, Dc, 1.0, J2, want_O=False)
+        assert sg[k] == ev.sign
+        assert abs(la[k] - ev.logabs) < 1e-10, (k, la[k], ev.logabs)
+        assert abs(el[k] - ev.eloc) < 1e-8 * eloc_scale(ev, sub[k]), (k, el[k], ev.eloc)
+
+
+def test_fullsize_mixed_energy_and_gradient_against_fp64(workload):
+    """Mixed path against the FP64 GPU path on 256 configurations of the
+    batch: energy per site within 1e-4, gradient cosine >= 0.999."""
+    A, spins = workload
+    S = packed(spins[:256])
+    res = {}
+    for prec in ("fp64", "mixed_tf32"):
+        p = make(A, prec)
+        g = p.gradient(S)
+        torch.cuda.synchronize()
+        res[prec] = (g["energy_per_site"], g["grad"].cpu().numpy().ravel(), g["n_used"])
+        p.close()
+    e64, g64, n64 = res["fp64"]
+    em, gm, nm = res["mixed_tf32"]
+    assert n64 == nm == 256
+    cos = gm @ g64 / (np.linalg.norm(gm) * np.linalg.norm(g64))
+    print("energy per site: fp64 %.8f mixed %.8f | gradient cosine %.6f" % (e64, em, cos))
+    assert abs(em - e64) < 1e-4
+    assert cos >= 0.999
