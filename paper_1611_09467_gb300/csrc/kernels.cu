@@ -1262,6 +1262,21 @@ int max_blocks_pair_tc() {
   prefer_shared(k_pair_tc, smem);
   cudaFuncSetAttribute(k_pair_tc, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pair_tc, kThreads, smem);
+  // The occupancy query reports one resident CTA for this kernel, although
+  // its registers and shared memory fit two (as ncu's occupancy section also
+  // shows); take the residency from the kernel's own attributes as well.
+  cudaFuncAttributes fa{};
+  int smem_sm = 0, reserved = 0, regs_sm = 0;
+  if (cudaFuncGetAttributes(&fa, k_pair_tc) == cudaSuccess &&
+      cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) == cudaSuccess &&
+      cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) == cudaSuccess &&
+      cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev) == cudaSuccess &&
+      fa.numRegs > 0) {
+    const size_t per_block = fa.sharedSizeBytes + smem + (size_t)reserved;
+    const int by_smem = (int)((size_t)smem_sm / per_block);
+    const int by_regs = regs_sm / (fa.numRegs * kThreads);
+    nb = std::max(nb, std::min(by_smem, by_regs));
+  }
   // each resident CTA holds kTmemCols of the SM's 512 TMEM columns
   nb = std::min(nb, 512 / tc::kTmemCols);
   return nsm * (nb < 1 ? 1 : nb);
