@@ -307,12 +307,13 @@ template <typename R>
 struct TruncWork {
   R* Wm;      // P x ldw
   int ldw;
+  R* Wg;      // P x ldw in global memory: the reflectors of the register-tiled path
   R* tau;     // 4 * Qmax: tau left, tau right, scale left, scale right
   R* t;       // 2 * Qmax off-diagonal of the Golub-Kahan form
   R* t2;      // squares of t
   R* lam;     // Kmax
   R* Z;       // Kmax x 2Qmax
-  R* lu;      // Kmax x 6 x 2Qmax
+  R* lu;      // Kmax x 6 x 2Qmax: inverse-iteration workspace when it is not in shared memory
   R* Ub;      // Qmax x Kmax (unused when Ubs is set)
   R* Uk;      // Pmax x Kmax compact copy of the result in global memory
   R* Ubs;     // Qmax x Kmax in shared memory (after the truncation matrix)
@@ -328,6 +329,7 @@ struct TruncWork {
 PEPS_HD size_t trunc_ws_elems(int pq, int kmax, bool with_wm) {
   size_t e = 0;
   if (with_wm) e += (size_t)pq * (pq + 1);
+  e += (size_t)pq * (pq + 1);             // Wg
   e += 4 * (size_t)pq + 2 * (size_t)pq * 2;   // tau + scale factors (4 pq), t, t2
   e += kmax;                              // lam
   e += (size_t)kmax * 2 * pq;             // Z
@@ -381,18 +383,21 @@ __device__ int sturm_count(const R* t2, int n2, R x, R pivmin) {
 // 1/pivtiny); the caller normalises the vectors.  The recurrences carry their
 // running values in registers; memory only receives the factors and reads
 // back values that do not depend on the running recurrence, so loads can be
-// issued ahead.  The workspace is interleaved across the K threads (element
-// i of thread k at i * K + k): lock-step accesses of a warp are contiguous.
+// issued ahead.  Workspace: four real arrays (reciprocal pivots, first
+// super-diagonal of U, multipliers of L, right-hand side) and one byte per
+// row for the interchanges, each interleaved across the K threads (element i
+// of thread k at i * K + k) so lock-step accesses of a warp are contiguous.
+// The second super-diagonal of U is t[i+1] where rows i, i+1 were
+// interchanged and zero otherwise, so it is not stored.
 template <typename R>
-__device__ void inverse_iteration(const R* t, int n2, R lam, R pivtiny, R* ws, int K, int k, R* z, int zs,
-                                  unsigned seed) {
+__device__ void inverse_iteration(const R* t, int n2, R lam, R pivtiny, R* wsR, unsigned char* wsP, int K, int k,
+                                  R* z, int zs, unsigned seed) {
   const size_t st = (size_t)n2 * K;
-  R* rdd = ws + k;       // reciprocal pivots of U
+  R* rdd = wsR + k;      // reciprocal pivots of U
   R* du = rdd + st;      // first super-diagonal of U
-  R* du2 = du + st;      // second super-diagonal of U
-  R* mult = du2 + st;    // multipliers of L
-  R* piv = mult + st;    // 1 where rows i, i+1 were interchanged
-  R* b = piv + st;       // right-hand side / solution
+  R* mult = du + st;     // multipliers of L
+  R* b = mult + st;      // right-hand side / solution
+  unsigned char* piv = wsP + k;   // 1 where rows i, i+1 were interchanged
 #define IX(i) ((size_t)(i) * K)
   unsigned h = seed * 2654435761u + 12345u;
   auto start = [&]() {
@@ -408,14 +413,13 @@ __device__ void inverse_iteration(const R* t, int n2, R lam, R pivtiny, R* ws, i
     R next_d = -lam;
     R next_u = i + 1 < n2 - 1 ? t[i + 1] : R(0);
     const R bn = start();
-    R d_i, u_i, u2_i, l;
+    R d_i, u_i, l;
     if (fabs(cur_d) >= fabs(sub)) {
       d_i = cur_d == R(0) ? pivtiny : cur_d;
       l = sub / d_i;
       u_i = cur_u;
-      u2_i = R(0);
       next_d -= l * cur_u;
-      piv[IX(i)] = R(0);
+      piv[IX(i)] = 0;
       b[IX(i)] = bi;
       bi = bn - l * bi;
     } else {
@@ -423,16 +427,14 @@ __device__ void inverse_iteration(const R* t, int n2, R lam, R pivtiny, R* ws, i
       d_i = sub;
       u_i = next_d;
       next_d = cur_u - l * next_d;
-      u2_i = next_u;
       next_u = -l * next_u;
-      piv[IX(i)] = R(1);
+      piv[IX(i)] = 1;
       b[IX(i)] = bn;
       bi = bi - l * bn;
     }
     if (fabs(d_i) < pivtiny) d_i = d_i < R(0) ? -pivtiny : pivtiny;
     rdd[IX(i)] = R(1) / d_i;
     du[IX(i)] = u_i;
-    du2[IX(i)] = u2_i;
     mult[IX(i)] = l;
     cur_d = next_d;
     cur_u = next_u;
@@ -440,7 +442,7 @@ __device__ void inverse_iteration(const R* t, int n2, R lam, R pivtiny, R* ws, i
   if (fabs(cur_d) < pivtiny) cur_d = cur_d < R(0) ? -pivtiny : pivtiny;
   rdd[IX(n2 - 1)] = R(1) / cur_d;
   du[IX(n2 - 1)] = R(0);
-  du2[IX(n2 - 1)] = R(0);
+  piv[IX(n2 - 1)] = 0;
   b[IX(n2 - 1)] = bi;
   R sc = R(1);   // scale of the current iterate still to be applied
   for (int it = 0; it < 2; ++it) {
@@ -451,7 +453,7 @@ __device__ void inverse_iteration(const R* t, int n2, R lam, R pivtiny, R* ws, i
       for (int i = 0; i < n2 - 1; ++i) {
         const R bn = b[IX(i + 1)] * sc;
         const R l = mult[IX(i)];
-        if (piv[IX(i)] == R(0)) {
+        if (piv[IX(i)] == 0) {
           b[IX(i)] = bf;
           bf = bn - l * bf;
         } else {
@@ -465,7 +467,8 @@ __device__ void inverse_iteration(const R* t, int n2, R lam, R pivtiny, R* ws, i
     R y1 = R(0), y2 = R(0), mx = R(0);
 #pragma unroll 4
     for (int i = n2 - 1; i >= 0; --i) {
-      const R y = (b[IX(i)] - du[IX(i)] * y1 - du2[IX(i)] * y2) * rdd[IX(i)];
+      const R du2 = (piv[IX(i)] != 0 && i + 1 < n2 - 1) ? t[i + 1] : R(0);
+      const R y = (b[IX(i)] - du[IX(i)] * y1 - du2 * y2) * rdd[IX(i)];
       b[IX(i)] = y;
       mx = fmax(mx, fabs(y));
       y2 = y1;
@@ -727,6 +730,9 @@ __device__ void cta_topk_left(const R* X, int m, int n, int K, TruncWork<R>& w, 
   bool tiled = false;
   if constexpr (sizeof(R) == 4) {
     if (P > 32 && P <= 128) {   // below 33 rows the shared-memory version is as fast
+      // the reflectors go to global memory: shared memory then holds the
+      // inverse-iteration workspace
+      W = w.Wg;
       bidiag_tiles_f32(X, n, tall, P, Q, W, ld, w.t, w.tau, w.Qmax);
       tiled = true;
     }
@@ -930,7 +936,15 @@ __device__ void cta_topk_left(const R* X, int m, int n, int K, TruncWork<R>& w, 
   PEPS_PHASE(2);
   // ---------------- inverse iteration, one thread per vector
   const R pivtiny = Eps<R>::eps * fmax(tmax, Eps<R>::tiny * R(1e10));
-  if (tid < K) inverse_iteration(w.t, n2, w.lam[tid], pivtiny, w.lu, K, tid, w.Z + tid, K, (unsigned)(tid + 1));
+  {
+    // in shared memory (the matrix buffer, free on the register-tiled path,
+    // and the Ub buffer for the interchange bytes) when it fits
+    const bool in_smem = tiled && (size_t)4 * n2 * K <= (size_t)w.Qmax * w.ldw;
+    R* wsR = in_smem ? w.Wm : w.lu;
+    unsigned char* wsP = in_smem ? reinterpret_cast<unsigned char*>(w.Ubs)
+                                 : reinterpret_cast<unsigned char*>(w.lu + (size_t)4 * n2 * K);
+    if (tid < K) inverse_iteration(w.t, n2, w.lam[tid], pivtiny, wsR, wsP, K, tid, w.Z + tid, K, (unsigned)(tid + 1));
+  }
   __syncthreads();
   PEPS_PHASE(3);
   // extract u-parts (odd positions) for a tall matrix, v-parts (even) for a wide one

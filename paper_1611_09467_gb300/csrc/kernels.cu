@@ -253,6 +253,7 @@ __device__ void carve_zip(const Geometry& g, R*& p, ZipBufs<R>& zb, R* wm_smem, 
   zb.X = p; p += P * P;
   TruncWork<R>& w = zb.tw;
   w.ldw = (int)P + 1;
+  w.Wg = p; p += P * (P + 1);
   R* sh = gsm;   // shared reals region: [Wm][Ubs][Uks]
   if (wm_smem) {
     w.Wm = sh;
