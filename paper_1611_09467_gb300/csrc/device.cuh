@@ -353,6 +353,21 @@ __device__ __forceinline__ void householder(R alpha, R ss, R& tau, R& scale, R& 
   }
 }
 
+// The same for FP32 with the hardware-approximate division (2 ulp): the
+// register-tiled bidiagonalisation forms these scalars on its critical path.
+__device__ __forceinline__ void householder_fast(float alpha, float ss, float& tau, float& scale, float& beta) {
+  if (ss <= 0.f) {
+    tau = 0.f;
+    scale = 0.f;
+    beta = alpha;
+  } else {
+    const float nrm = sqrtf(alpha * alpha + ss);
+    beta = alpha >= 0.f ? -nrm : nrm;
+    tau = __fdividef(beta - alpha, beta);
+    scale = __fdividef(1.f, alpha - beta);
+  }
+}
+
 __device__ __forceinline__ double sturm_div(double a, double b) { return a / b; }
 __device__ __forceinline__ float sturm_div(float a, float b) { return __fdividef(a, b); }
 
@@ -567,7 +582,7 @@ static __device__ __noinline__ void bidiag_tiles_f32(const float* X, int n, bool
           for (int o = 8; o >= 1; o >>= 1) ss += __shfl_xor_sync(hmask, ss, o);
           const float alpha = __shfl_sync(hmask, sel8(col, jj), (lane & 16) | tb);
           float tau, scale, beta;
-          householder(alpha, ss, tau, scale, beta);
+          householder_fast(alpha, ss, tau, scale, beta);
 #pragma unroll
           for (int r = 0; r < 8; ++r) {
             const int i = r0 + r;
@@ -632,7 +647,7 @@ static __device__ __noinline__ void bidiag_tiles_f32(const float* X, int n, bool
 #pragma unroll
           for (int q = 0; q < 16; ++q) ssr += sc[2 + q];
           float tr, sr, br;
-          householder(sc[1], ssr, tr, sr, br);
+          householder_fast(sc[1], ssr, tr, sr, br);
           if (tid == 0) {
             t[2 * j + 1] = br;
             tau4[qm + j] = tr;
@@ -954,8 +969,66 @@ __device__ void cta_topk_left(const R* X, int m, int n, int K, TruncWork<R>& w, 
     Ub[e] = w.Z[(size_t)(2 * i + (tall ? 1 : 0)) * K + k];
   }
   __syncthreads();
-  // ---------------- Gram-Schmidt with re-orthogonalisation (CGS2)
-  for (int j = 0; j < K; ++j) {
+  // ---------------- orthonormal basis of the kept vectors: CholeskyQR2
+  // (G = Ub^T Ub = R^T R, Ub <- Ub R^-1, twice; Fukaya et al. 2014).  Each
+  // pass costs three barriers.  If a direction of Ub is below 1e-3 of its
+  // norm (a cluster or a zero singular value), Gram-Schmidt with replacement
+  // of degenerate directions (below) takes over from the current Ub.
+  bool need_cgs = false;
+  {
+    __shared__ int cq_bad;
+    R* G = w.Uks;   // K x K, free until the back-transformation
+    for (int pass = 0; pass < 2 && !need_cgs; ++pass) {
+      for (int e = tid; e < K * K; e += blockDim.x) {
+        const int a = e / K, b = e % K;
+        if (b < a) continue;
+        R sacc = R(0);
+        for (int i = 0; i < Q; ++i) sacc += Ub[i * K + a] * Ub[i * K + b];
+        G[e] = sacc;
+      }
+      __syncthreads();
+      if (warp == 0) {
+        // right-looking Cholesky of the upper triangle in place; lane l owns column l
+        const R d0 = lane < K ? G[lane * K + lane] : R(0);
+        int bad = 0;
+        for (int j = 0; j < K && !bad; ++j) {
+          const R d = G[j * K + j];
+          const R dj0 = __shfl_sync(0xffffffffu, d0, j);
+          if (!(d > R(1e-6) * dj0) || !(dj0 > R(0))) {
+            bad = 1;
+            break;
+          }
+          const R r = dsqrt(d);
+          __syncwarp();
+          if (lane > j && lane < K) G[j * K + lane] /= r;
+          __syncwarp();
+          if (lane == j) G[j * K + j] = r;
+          if (lane > j && lane < K) {
+            const R gjl = G[j * K + lane];
+            for (int mm = j + 1; mm <= lane; ++mm) G[mm * K + lane] -= G[j * K + mm] * gjl;
+          }
+          __syncwarp();
+        }
+        if (lane == 0) cq_bad = bad;
+      }
+      __syncthreads();
+      if (cq_bad) {
+        need_cgs = true;
+        break;
+      }
+      // Ub <- Ub R^-1, one thread per row (forward substitution in place)
+      for (int i = tid; i < Q; i += blockDim.x) {
+        for (int l = 0; l < K; ++l) {
+          R x = Ub[i * K + l];
+          for (int k = 0; k < l; ++k) x -= Ub[i * K + k] * G[k * K + l];
+          Ub[i * K + l] = x / G[l * K + l];
+        }
+      }
+      __syncthreads();
+    }
+  }
+  // ---------------- Gram-Schmidt with re-orthogonalisation (CGS2), fallback
+  for (int j = 0; j < K && need_cgs; ++j) {
     for (int attempt = 0; attempt <= Q; ++attempt) {
       R s = R(0);
       for (int i = tid; i < Q; i += blockDim.x) s += Ub[i * K + j] * Ub[i * K + j];
