@@ -368,6 +368,8 @@ __device__ __forceinline__ void householder_fast(float alpha, float ss, float& t
   }
 }
 
+// Division inside the Sturm counts: IEEE in FP64, the hardware approximation
+// (2 ulp) in FP32, where it sits on a long dependent chain.
 __device__ __forceinline__ double sturm_div(double a, double b) { return a / b; }
 __device__ __forceinline__ float sturm_div(float a, float b) { return __fdividef(a, b); }
 

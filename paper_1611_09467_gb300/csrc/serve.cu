@@ -4,11 +4,14 @@
 // the kernels of concurrent requests run side by side.
 // A request asks for ln|psi|, E_loc and/or Delta of a batch of configurations
 // of one model (a context: lattice, D, Dc, tensors).  The server runs
-// requests on `nlanes` lanes, each a CUDA stream with its own worker
-// context (same model buffers, private workspace), so requests of different
-// models and sizes overlap on the GPU.  Requests wait in a queue until a lane
-// is free and the HBM they need fits under the budget (footprint admission);
-// a request that does not fit lets smaller queued ones pass.  Completion is
+// requests on `nlanes` lanes, each a CUDA stream with worker contexts (the
+// model's buffers, private workspaces), so requests of different models and
+// sizes overlap on the GPU.  A lane keeps one worker per model it
+// has served (least recently used first), so switching models does not
+// rebuild workspaces; idle workers are freed only when the budget requires.
+// Requests wait in a queue until a lane is free and the HBM they need fits
+// under the budget (footprint admission); a request that does not fit lets
+// smaller queued ones pass.  Completion is
 // observed through one event per lane; the latency of a request runs from
 // submission to the poll that sees its event.  Results do not depend on the
 // lane or on what else runs: every configuration is evaluated by the same
@@ -47,8 +50,8 @@ struct Lane {
   cudaEvent_t done = nullptr;
   bool busy = false;
   Request req{};
-  peps_ctx* model = nullptr;   // model of the worker below
-  peps_ctx* worker = nullptr;
+  // worker contexts of this lane, one per model, least recently used first
+  std::vector<std::pair<peps_ctx*, peps_ctx*>> workers;
 };
 
 }  // namespace
@@ -70,30 +73,70 @@ namespace {
 size_t in_use(const peps_server* s) {
   size_t b = 0;
   for (const Lane& l : s->lanes)
-    if (l.worker) b += peps::ctx_workspace_bytes(l.worker);
+    for (const auto& w : l.workers) b += peps::ctx_workspace_bytes(w.second);
   return b;
+}
+
+int find_worker(const Lane& l, const peps_ctx* model) {
+  for (size_t k = 0; k < l.workers.size(); ++k)
+    if (l.workers[k].first == model) return (int)k;
+  return -1;
 }
 
 // Bytes a lane would add to run request r (workspace growth, or a new worker).
 size_t extra_bytes(const peps_server* s, const Lane& l, const Request& r) {
   const size_t need = peps::ctx_footprint(r.model, r.n, s->lane_gb, (int)s->lanes.size());
-  if (l.worker && l.model == r.model) {
-    const size_t have = peps::ctx_workspace_bytes(l.worker);
+  const int k = find_worker(l, r.model);
+  if (k >= 0) {
+    const size_t have = peps::ctx_workspace_bytes(l.workers[k].second);
     return need > have ? need - have : 0;
   }
   return need;
 }
 
-peps_status launch(peps_server* s, Lane& l, const Request& r) {
-  if (!l.worker || l.model != r.model) {
-    if (l.worker) {
-      cudaStreamSynchronize(l.stream);
-      peps_destroy(l.worker);
+// Frees least recently used workers of idle lanes (never `keep`) until
+// `extra` more bytes fit under the budget; returns whether they do.  Freeing
+// device memory synchronises the device, so this only runs when the budget
+// requires it.
+bool make_room(peps_server* s, size_t extra, const peps_ctx* keep) {
+  while (in_use(s) + extra > s->budget) {
+    Lane* victim_lane = nullptr;
+    for (Lane& l : s->lanes) {
+      if (l.busy) continue;
+      for (const auto& w : l.workers)
+        if (w.second != keep) {
+          victim_lane = &l;
+          break;
+        }
+      if (victim_lane) break;
     }
-    l.worker = peps::ctx_clone(r.model, l.stream, s->lane_gb, (int)s->lanes.size());
-    l.model = r.model;
+    if (!victim_lane) return false;
+    for (auto it = victim_lane->workers.begin(); it != victim_lane->workers.end(); ++it)
+      if (it->second != keep) {
+        cudaStreamSynchronize(victim_lane->stream);
+        peps_destroy(it->second);
+        victim_lane->workers.erase(it);
+        break;
+      }
   }
-  const peps_status st = peps_evaluate(l.worker, r.S, r.n, r.logabs, r.sign, r.eloc, r.O, r.status);
+  return true;
+}
+
+peps_status launch(peps_server* s, Lane& l, const Request& r) {
+  int k = find_worker(l, r.model);
+  if (k < 0) {
+    peps_ctx* w = peps::ctx_clone(r.model, l.stream, s->lane_gb, (int)s->lanes.size());
+    if (!w) return PEPS_ENOMEM;
+    l.workers.emplace_back(r.model, w);
+    k = (int)l.workers.size() - 1;
+  } else if (k != (int)l.workers.size() - 1) {
+    const auto w = l.workers[k];   // most recently used goes last
+    l.workers.erase(l.workers.begin() + k);
+    l.workers.push_back(w);
+    k = (int)l.workers.size() - 1;
+  }
+  peps_ctx* worker = l.workers[k].second;
+  const peps_status st = peps_evaluate(worker, r.S, r.n, r.logabs, r.sign, r.eloc, r.O, r.status);
   if (st != PEPS_OK) return st;
   if (cudaEventRecord(l.done, l.stream) != cudaSuccess) return PEPS_ECUDA;
   l.busy = true;
@@ -119,12 +162,12 @@ peps_status step(peps_server* s) {
     Lane* free_lane = nullptr;
     // prefer a free lane that already holds a worker of this model
     for (Lane& l : s->lanes)
-      if (!l.busy && (!free_lane || (l.model == it->model && free_lane->model != it->model))) free_lane = &l;
+      if (!l.busy && (!free_lane || (find_worker(l, it->model) >= 0 && find_worker(*free_lane, it->model) < 0)))
+        free_lane = &l;
     if (!free_lane) break;
     const size_t extra = extra_bytes(s, *free_lane, *it);
-    size_t freed = 0;
-    if (free_lane->worker && free_lane->model != it->model) freed = peps::ctx_workspace_bytes(free_lane->worker);
-    if (in_use(s) - freed + extra > s->budget) {
+    const int k = find_worker(*free_lane, it->model);
+    if (!make_room(s, extra, k >= 0 ? free_lane->workers[k].second : nullptr)) {
       ++it;   // does not fit now: let a smaller queued request pass
       continue;
     }
@@ -173,7 +216,8 @@ peps_status peps_server_destroy(peps_server* s) {
   if (!s) return PEPS_OK;
   for (Lane& l : s->lanes) {
     if (l.stream) cudaStreamSynchronize(l.stream);
-    if (l.worker) peps_destroy(l.worker);
+    for (auto& w : l.workers) peps_destroy(w.second);
+    l.workers.clear();
     if (l.done) cudaEventDestroy(l.done);
     if (l.stream) cudaStreamDestroy(l.stream);
   }
