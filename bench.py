@@ -34,6 +34,13 @@ METRIC = "configs/s (psi+E_loc+dln psi) 16x16 D=8 Dc=16, mixed vs plain FP32; p9
 UNIT = "configs/s"
 FP32_SIMT_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per configuration
+# of the dominant kernel, from one ncu capture of 32 configurations of the
+# same kernel build (2 launches: 192.7 and 190.1 MB); traffic grows in
+# proportion to the configurations a launch processes.  It describes that
+# build only: re-measure it, or drop the entry, when the kernel changes.
+DRAM_BYTES_PER_CONFIG = {("16x16_D8_Dc16", "float", "boundary"): 5.98e6}
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -231,8 +238,12 @@ def run_ours(args, rank, world, local_rank):
     if f_cfg is not None:
         flops_per_launch = f_cfg * n * args.steps / launches_top
         achieved = flops_per_launch / (ms_top / launches_top / 1e3) / 1e12
+        cfg_per_launch = n * args.steps / launches_top
+        bpc = DRAM_BYTES_PER_CONFIG.get((args.workload, "float" if args.prec != "fp64" else "double", top))
         roofline = {"bound": "alu", "kernel": top, "achieved": achieved, "peak": FP32_SIMT_TFLOPS,
-                    "unit": "TFLOP/s", "frac": achieved / FP32_SIMT_TFLOPS, "traffic": None,
+                    "unit": "TFLOP/s", "frac": achieved / FP32_SIMT_TFLOPS,
+                    "traffic": bpc * cfg_per_launch if bpc else None,
+                    "traffic_unit": "bytes per launch (DRAM read + write, ncu)",
                     "peak_source": "FP32 SIMT: 152 SMs x 128 lanes x 2 flop x 2070 MHz (derived, nominal)",
                     "flops_per_config": f_cfg}
     share = {k: round(v[0] / sum(x[0] for x in kern.values()), 4) for k, v in kern.items()}
