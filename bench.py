@@ -50,8 +50,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="16x16_D8_Dc16")
     ap.add_argument("--prec", default="mixed_tf32", choices=["fp32", "fp64", "mixed_tf32"])
-    ap.add_argument("--compare-fp32", action="store_true",
-                    help="also time the plain FP32 path (1 warm-up, 1 step) on the same workload")
+    ap.add_argument("--compare-fp32", action=argparse.BooleanOptionalAction, default=True,
+                    help="also time the plain FP32 path (1 warm-up, 1 step) on the same configurations")
     ap.add_argument("--n", type=int, default=0, help="batch override (probes only; the metric uses the default)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
