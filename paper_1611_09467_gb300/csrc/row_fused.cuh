@@ -36,14 +36,16 @@ struct RowSmem {
   static constexpr int MD = D * Dc;        // one slice of Md
   static constexpr int P = DD * Dc;        // P[(yi,u)][xo]
   static constexpr int Q = D * Dc * D;     // Q[d][(xo,yo)]
-  static constexpr int step_total = MU + T + 2 * (FS + MD) + P + Q;   // F and Md slices double-buffered
-  static constexpr int env_total = MU + Dc * FS + MD + FS + 2 * Dc * DD;
+  // slices are taken in pairs; the F and Md slices of consecutive pairs alternate
+  static constexpr int step_total = MU + T + 4 * (FS + MD) + 2 * P + 2 * Q;
+  static constexpr int env_total = MU + Dc * FS + 2 * (MD + FS) + 4 * Dc * DD;
   static constexpr int total = step_total > env_total ? step_total : env_total;
   static constexpr int OUT = Dc * D * Dc;  // outputs of a step
   static constexpr int OPT = (OUT + kThreads - 1) / kThreads;   // outputs per thread
   static constexpr int TM = (DD + 3) / 4;  // 4x4 tiles of the site-env accumulator per dimension
   static constexpr int TPT = (TM * TM + kThreads - 1) / kThreads;
   static_assert(D4 <= env_total, "site environment staging must fit the site-env buffers");
+  static_assert(Dc % 2 == 0, "slices are processed in pairs");
 };
 
 // One fused single-row transfer step.  right == false: F_{c-1} -> F_c;
@@ -61,10 +63,10 @@ __device__ R row_step_fused(bool right, const R* Fin, R* __restrict__ Fout, cons
   constexpr int DD = S::DD, D3 = S::D3, XY = Dc * D;
   R* Mus = sm;
   R* Ts = Mus + S::MU;
-  R* Fs0 = Ts + S::T;
-  R* Mds0 = Fs0 + 2 * S::FS;
-  R* Pb = Mds0 + 2 * S::MD;
-  R* Qb = Pb + S::P;
+  R* Fs0 = Ts + S::T;             // 4 F slices: pair parity x slice in pair
+  R* Mds0 = Fs0 + 4 * S::FS;      // 4 Md slices
+  R* Pb0 = Mds0 + 4 * S::MD;      // 2 P blocks (slice in pair)
+  R* Qb0 = Pb0 + 2 * S::P;        // 2 Q blocks
   const int tid = threadIdx.x;
   __syncthreads();
   for (int e = tid; e < S::T; e += kThreads) {
@@ -81,36 +83,54 @@ __device__ R row_step_fused(bool right, const R* Fin, R* __restrict__ Fout, cons
   R acc[S::OPT];
 #pragma unroll
   for (int q = 0; q < S::OPT; ++q) acc[q] = R(0);
-  // three barriers per slice: the slice buffers alternate, so loading slice
-  // s+1 cannot overwrite what s3 of slice s still reads
-  for (int s = 0; s < Dc; ++s) {
-    R* Fs = Fs0 + (s & 1) * S::FS;
-    R* Mds = Mds0 + (s & 1) * S::MD;
-    for (int e = tid; e < S::FS; e += kThreads) Fs[e] = Fin[s * XY + e];   // [xi][yi]
-    for (int e = tid; e < S::MD; e += kThreads) {
-      const int d = e / Dc, xo = e % Dc;
-      Mds[e] = right ? Md[xo * D * Dc + d * Dc + s] : Md[s * D * Dc + d * Dc + xo];
+  // three barriers per pair of slices: the slice buffers of consecutive pairs
+  // alternate, so loading pair p+1 cannot overwrite what s3 of pair p reads
+  for (int s0 = 0; s0 < Dc; s0 += 2) {
+    const int par = (s0 >> 1) & 1;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int s = s0 + h;
+      R* Fs = Fs0 + (2 * par + h) * S::FS;
+      R* Mds = Mds0 + (2 * par + h) * S::MD;
+      for (int e = tid; e < S::FS; e += kThreads) Fs[e] = Fin[s * XY + e];   // [xi][yi]
+      for (int e = tid; e < S::MD; e += kThreads) {
+        const int d = e / Dc, xo = e % Dc;
+        Mds[e] = right ? Md[xo * D * Dc + d * Dc + s] : Md[s * D * Dc + d * Dc + xo];
+      }
     }
     __syncthreads();
-    smem_gemm_km<R, D, D * Dc, Dc>(Fs, Mus, [&](int i, int j, R v) {
-      const int u = j / Dc, xo = j % Dc;      // i = yi, j = (u, xo)
-      Pb[(i * D + u) * Dc + xo] = v;
-    });
-    __syncthreads();
-    smem_gemm_km<R, Dc, DD, DD>(Pb, Ts, [&](int i, int j, R v) {
-      const int yo = j / D, d = j % D;        // i = xo, j = (yo, d)
-      Qb[d * XY + i * D + yo] = v;
-    });
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      R* Pb = Pb0 + h * S::P;
+      smem_gemm_km<R, D, D * Dc, Dc>(Fs0 + (2 * par + h) * S::FS, Mus, [&](int i, int j, R v) {
+        const int u = j / Dc, xo = j % Dc;      // i = yi, j = (u, xo)
+        Pb[(i * D + u) * Dc + xo] = v;
+      });
+    }
     __syncthreads();
 #pragma unroll
-    for (int q = 0; q < S::OPT; ++q) {
-      const int o = q * kThreads + tid;
-      if (S::OUT % kThreads == 0 || o < S::OUT) {
-        const int row = o % XY, xo2 = o / XY;
-        R v = acc[q];
+    for (int h = 0; h < 2; ++h) {
+      R* Qb = Qb0 + h * S::Q;
+      smem_gemm_km<R, Dc, DD, DD>(Pb0 + h * S::P, Ts, [&](int i, int j, R v) {
+        const int yo = j / D, d = j % D;        // i = xo, j = (yo, d)
+        Qb[d * XY + i * D + yo] = v;
+      });
+    }
+    __syncthreads();
 #pragma unroll
-        for (int d = 0; d < D; ++d) v = fma(Qb[d * XY + row], Mds[d * Dc + xo2], v);
-        acc[q] = v;
+    for (int h = 0; h < 2; ++h) {
+      const R* Qb = Qb0 + h * S::Q;
+      const R* Mds = Mds0 + (2 * par + h) * S::MD;
+#pragma unroll
+      for (int q = 0; q < S::OPT; ++q) {
+        const int o = q * kThreads + tid;
+        if (S::OUT % kThreads == 0 || o < S::OUT) {
+          const int row = o % XY, xo2 = o / XY;
+          R v = acc[q];
+#pragma unroll
+          for (int d = 0; d < D; ++d) v = fma(Qb[d * XY + row], Mds[d * Dc + xo2], v);
+          acc[q] = v;
+        }
       }
     }
   }
@@ -150,10 +170,10 @@ __device__ void site_env_fused(const R* F, const R* __restrict__ Mu, const R* __
   constexpr int DD = S::DD, D3 = S::D3, XY = Dc * D, TM = S::TM;
   R* Mus = sm;                 // Mu as stored: [a][(u,b)]
   R* Gs = Mus + S::MU;         // G: [b'][(b,r)]
-  R* Mdk = Gs + Dc * XY;       // slice s of Md: [b'][d]
-  R* Fs = Mdk + S::MD;         // slice s of F: [a][l]
-  R* Xs = Fs + S::FS;          // [b][(l,u)]
-  R* Ys = Xs + Dc * DD;        // [b][(d,r)]
+  R* Mdk0 = Gs + Dc * XY;      // two slices of Md: [b'][d]
+  R* Fs0 = Mdk0 + 2 * S::MD;   // two slices of F: [a][l]
+  R* Xs0 = Fs0 + 2 * S::FS;    // two [b][(l,u)]
+  R* Ys0 = Xs0 + 2 * Dc * DD;  // two [b][(d,r)]
   const int tid = threadIdx.x;
   __syncthreads();
   for (int e = tid; e < S::MU; e += kThreads) Mus[e] = Mu[e];
@@ -165,34 +185,53 @@ __device__ void site_env_fused(const R* F, const R* __restrict__ Mu, const R* __
     for (int i = 0; i < 4; ++i)
 #pragma unroll
       for (int j = 0; j < 4; ++j) acc[t][i][j] = R(0);
-  for (int s = 0; s < Dc; ++s) {
-    for (int e = tid; e < S::MD; e += kThreads) {
-      const int bp = e / D, d = e % D;
-      Mdk[e] = Md[s * D * Dc + d * Dc + bp];
+  // three barriers per pair of slices of a'
+  for (int s0 = 0; s0 < Dc; s0 += 2) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int s = s0 + h;
+      R* Mdk = Mdk0 + h * S::MD;
+      R* Fs = Fs0 + h * S::FS;
+      for (int e = tid; e < S::MD; e += kThreads) {
+        const int bp = e / D, d = e % D;
+        Mdk[e] = Md[s * D * Dc + d * Dc + bp];
+      }
+      for (int e = tid; e < S::FS; e += kThreads) Fs[e] = F[s * XY + e];
     }
-    for (int e = tid; e < S::FS; e += kThreads) Fs[e] = F[s * XY + e];
     __syncthreads();
     // X: rows l, cols (u, b), k = a;  Y: rows d, cols (b, r), k = b'
-    smem_gemm_km<R, D, D * Dc, Dc>(Fs, Mus, [&](int i, int j, R v) { Xs[(j % Dc) * DD + i * D + j / Dc] = v; });
-    smem_gemm_km<R, D, Dc * D, Dc>(Mdk, Gs, [&](int i, int j, R v) { Ys[(j / D) * DD + i * D + j % D] = v; });
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      R* Xs = Xs0 + h * Dc * DD;
+      R* Ys = Ys0 + h * Dc * DD;
+      smem_gemm_km<R, D, D * Dc, Dc>(Fs0 + h * S::FS, Mus,
+                                     [&](int i, int j, R v) { Xs[(j % Dc) * DD + i * D + j / Dc] = v; });
+      smem_gemm_km<R, D, Dc * D, Dc>(Mdk0 + h * S::MD, Gs,
+                                     [&](int i, int j, R v) { Ys[(j / D) * DD + i * D + j % D] = v; });
+    }
     __syncthreads();
 #pragma unroll
-    for (int t = 0; t < S::TPT; ++t) {
-      const int tile = t * kThreads + tid;
-      if ((TM * TM) % kThreads == 0 || tile < TM * TM) {
-        const int i0 = (tile / TM) * 4, j0 = (tile % TM) * 4;
+    for (int h = 0; h < 2; ++h) {
+      const R* Xs = Xs0 + h * Dc * DD;
+      const R* Ys = Ys0 + h * Dc * DD;
+#pragma unroll
+      for (int t = 0; t < S::TPT; ++t) {
+        const int tile = t * kThreads + tid;
+        if ((TM * TM) % kThreads == 0 || tile < TM * TM) {
+          const int i0 = (tile / TM) * 4, j0 = (tile % TM) * 4;
 #pragma unroll 4
-        for (int b = 0; b < Dc; ++b) {
-          R xv[4], yv[4];
+          for (int b = 0; b < Dc; ++b) {
+            R xv[4], yv[4];
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            xv[q] = (DD % 4 == 0 || i0 + q < DD) ? Xs[b * DD + i0 + q] : R(0);
-            yv[q] = (DD % 4 == 0 || j0 + q < DD) ? Ys[b * DD + j0 + q] : R(0);
+            for (int q = 0; q < 4; ++q) {
+              xv[q] = (DD % 4 == 0 || i0 + q < DD) ? Xs[b * DD + i0 + q] : R(0);
+              yv[q] = (DD % 4 == 0 || j0 + q < DD) ? Ys[b * DD + j0 + q] : R(0);
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+              for (int j = 0; j < 4; ++j) acc[t][i][j] = fma(xv[i], yv[j], acc[t][i][j]);
           }
-#pragma unroll
-          for (int i = 0; i < 4; ++i)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) acc[t][i][j] = fma(xv[i], yv[j], acc[t][i][j]);
         }
       }
     }
