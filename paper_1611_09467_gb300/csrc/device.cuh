@@ -634,15 +634,21 @@ static __device__ __noinline__ void bidiag_tiles_f32(const float* X, int n, bool
           // ---- right reflector on row j (columns j+1..Q-1)
           const int ja = (jj + 1) & 7;       // local column of j+1
           const int ta = (j + 1) >> 3;       // its tile column
+          // warp-uniform: some column of this warp lies right of j.  A warp
+          // whose columns all lie left of j has a zero share of the row norm
+          // and of W u, and nothing to update, so it skips both.
+          const bool act = warp * 16 + 15 > j;
           float row[8];
-          row_of(a, jj, row);
+          if (act) row_of(a, jj, row);
           if (ti == tb) {
             float ss = 0.f;
+            if (act) {
 #pragma unroll
-            for (int c = 0; c < 8; ++c)
-              if (c0 + c > j + 1) ss = fmaf(row[c], row[c], ss);
+              for (int c = 0; c < 8; ++c)
+                if (c0 + c > j + 1) ss = fmaf(row[c], row[c], ss);
+              if (tj == ta) sc[1] = sel8(row, ja);
+            }
             sc[2 + tj] = ss;
-            if (tj == ta) sc[1] = sel8(row, ja);
           }
           __syncthreads();
           float ssr = 0.f;
@@ -655,18 +661,17 @@ static __device__ __noinline__ void bidiag_tiles_f32(const float* X, int n, bool
             tau4[qm + j] = tr;
             tau4[3 * qm + j] = sr;
           }
-          const bool act = warp * 16 + 15 > j;   // warp-uniform: some u entry of this warp is non-zero
           float2 u[4];
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const float2 x = make_float2(__shfl_sync(0xffffffffu, row[2 * q], (lane & 16) | tb),
-                                         __shfl_sync(0xffffffffu, row[2 * q + 1], (lane & 16) | tb));
-            const int c = c0 + 2 * q;
-            u[q].x = c == j + 1 ? 1.f : (c > j + 1 ? sr * x.x : 0.f);
-            u[q].y = c + 1 == j + 1 ? 1.f : (c + 1 > j + 1 ? sr * x.y : 0.f);
-          }
           float z[8];
           if (act) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const float2 x = make_float2(__shfl_sync(0xffffffffu, row[2 * q], (lane & 16) | tb),
+                                           __shfl_sync(0xffffffffu, row[2 * q + 1], (lane & 16) | tb));
+              const int c = c0 + 2 * q;
+              u[q].x = c == j + 1 ? 1.f : (c > j + 1 ? sr * x.x : 0.f);
+              u[q].y = c + 1 == j + 1 ? 1.f : (c + 1 > j + 1 ? sr * x.y : 0.f);
+            }
 #pragma unroll
             for (int r = 0; r < 8; ++r) {
               float2 s = make_float2(0.f, 0.f);
@@ -676,13 +681,10 @@ static __device__ __noinline__ void bidiag_tiles_f32(const float* X, int n, bool
             }
 #pragma unroll
             for (int r = 0; r < 8; ++r) z[r] += __shfl_xor_sync(0xffffffffu, z[r], 16);
-          } else {
-#pragma unroll
-            for (int r = 0; r < 8; ++r) z[r] = 0.f;
-          }
-          if (lane < 16) {
-            *reinterpret_cast<float4*>(zp + warp * 128 + r0) = make_float4(z[0], z[1], z[2], z[3]);
-            *reinterpret_cast<float4*>(zp + warp * 128 + r0 + 4) = make_float4(z[4], z[5], z[6], z[7]);
+            if (lane < 16) {
+              *reinterpret_cast<float4*>(zp + warp * 128 + r0) = make_float4(z[0], z[1], z[2], z[3]);
+              *reinterpret_cast<float4*>(zp + warp * 128 + r0 + 4) = make_float4(z[4], z[5], z[6], z[7]);
+            }
           }
           __syncthreads();
           if (act) {
@@ -690,6 +692,7 @@ static __device__ __noinline__ void bidiag_tiles_f32(const float* X, int n, bool
             for (int r = 0; r < 8; ++r) z[r] = 0.f;
 #pragma unroll
             for (int q = 0; q < kWarps; ++q) {
+              if (q * 16 + 15 <= j) continue;   // that warp's share is zero and was not written
               const float4 p0 = *reinterpret_cast<const float4*>(zp + q * 128 + r0);
               const float4 p1 = *reinterpret_cast<const float4*>(zp + q * 128 + r0 + 4);
               z[0] += p0.x; z[1] += p0.y; z[2] += p0.z; z[3] += p0.w;
