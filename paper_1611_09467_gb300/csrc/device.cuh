@@ -932,7 +932,8 @@ __device__ void cta_topk_left(const R* X, int m, int n, int K, TruncWork<R>& w, 
     const int gid = tid / G, gl = tid % G;
     const int gbase = (lane / G) * G;
     const double lg = log((double)(G + 1));
-    const int nit = (int)((Eps<R>::bits + 2) * 0.6931471805599453 / lg) + 2;
+    // (G+1)^nit >= 2^(bits+2): the final interval is below a quarter ulp of the bound
+    const int nit = (int)((Eps<R>::bits + 2) * 0.6931471805599453 / lg) + 1;
     const int idx = n2 - 1 - gid;  // ascending index of the (gid+1)-th largest eigenvalue
     R lo = R(0), hi = bound;
     for (int it = 0; it < nit; ++it) {
