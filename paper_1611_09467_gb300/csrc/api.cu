@@ -278,8 +278,6 @@ peps_status ensure_workspace(peps_ctx* c, int n, bool want_O) {
   return PEPS_OK;
 }
 
-bool same_precision_double(const peps_ctx* c) { return c->p.prec == PEPS_FP64; }
-
 template <typename R>
 KArgs<R> make_args(peps_ctx* c, const uint64_t* S, int n, const Small& sm) {
   KArgs<R> a;
