@@ -78,6 +78,41 @@ def test_tensor_generator_layout():
         assert abs(c * c * (raw_norm ** 2 + 2 * a[0] * raw_norm + 1) - raw_norm ** 2) < 1e-10 * raw_norm ** 2
 
 
+def test_near_product_generator():
+    """Near-product tensors: edge bonds of dimension one, unit norm per site,
+    deterministic; the all-zero-bond entries of the two spin components are
+    in the ratio sin t : cos t with t in [pi/8, 3pi/8] up to the noise (whose
+    expected norm equals the product part's), and the noise is the same keyed
+    draw as the i.i.d. recipe scaled by eta / sqrt(d D^4)."""
+    Ly, Lx, D = 3, 4, 3
+    A = inputs.near_product_tensors(Ly, Lx, D, seed=9)
+    N = Ly * Lx
+    assert A.shape == (N, 2, D, D, D, D)
+    assert np.array_equal(A, inputs.near_product_tensors(Ly, Lx, D, seed=9))
+    assert np.allclose(np.sqrt((A.reshape(N, -1) ** 2).sum(axis=1)), 1.0, atol=1e-14)
+    assert np.all(A[0, :, 1:] == 0) and np.all(A[0, :, :, :, 1:] == 0)
+    assert np.all(A[N - 1, :, :, 1:] == 0) and np.all(A[N - 1, :, :, :, :, 1:] == 0)
+    # without noise the tensors are exactly the product state
+    P = inputs.near_product_tensors(Ly, Lx, D, seed=9, eta=0.0)
+    t = np.arctan2(P[:, 1, 0, 0, 0, 0], P[:, 0, 0, 0, 0, 0])
+    assert np.all((t >= np.pi / 8 - 1e-12) & (t <= 3 * np.pi / 8 + 1e-12))
+    assert np.allclose(P[:, 0, 0, 0, 0, 0] ** 2 + P[:, 1, 0, 0, 0, 0] ** 2, 1.0)
+    rest = P.copy()
+    rest[:, :, 0, 0, 0, 0] = 0
+    assert np.all(rest == 0)
+    # the noise is the keyed i.i.d. draw, scaled (compare before normalisation)
+    eta = 0.7
+    B = inputs.near_product_tensors(Ly, Lx, D, seed=9, eta=eta)
+    G = inputs.make_tensors(Ly, Lx, D, seed=9)   # i.i.d. draw, normalised per site
+    for i in range(N):
+        b, g = B[i].reshape(-1).copy(), G[i].reshape(-1).copy()
+        b[0] = g[0] = 0.0
+        b[D ** 4] = g[D ** 4] = 0.0              # the all-zero-bond entry of s = 1
+        nz = g != 0
+        r = b[nz] / g[nz]
+        assert np.allclose(r, r[0], rtol=1e-12)
+
+
 # ------------------------------------------------------------- P-a: ED pins
 
 def test_ed_2x2_closed_form():
