@@ -697,7 +697,7 @@ __global__ void __launch_bounds__(kThreads) k_pair_fused(KArgs<R> a) {
 // inputs with FP32 accumulation.  Each CTA holds kTmemCols TMEM columns for
 // its lifetime; a timed-out wait marks the configuration and ends the CTA
 // after releasing TMEM.
-__global__ void __launch_bounds__(kThreads) k_pair_tc(KArgs<float> a) {
+__global__ void __launch_bounds__(kThreads, 2) k_pair_tc(KArgs<float> a) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ float red[64];
   __shared__ uint64_t sp[kMaxWords];

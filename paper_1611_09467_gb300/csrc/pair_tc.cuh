@@ -214,24 +214,32 @@ __device__ float pair_step_tc(PairTc& st, bool right, const float* Ein, float* _
       return 0.f;
     }
   }
-  for (int s = 0; s < Dc; ++s) {
-    // ---- B1 = Ein slice as [n = (y1i, y2i)][k = xi]; B4 = Md slice as [x'o][d2]
-    {
-      const int n = tid >> 2, xq = (tid & 3) * 4;
-      const float* src = Ein + s * (Dc * 64) + n;
-      st4(B1 + tc::kmaj(n, xq, 16), tc::to_tf32(src[(xq + 0) * 64]), tc::to_tf32(src[(xq + 1) * 64]),
-          tc::to_tf32(src[(xq + 2) * 64]), tc::to_tf32(src[(xq + 3) * 64]));
-    }
+  // Slice s+1 of Ein and Md is loaded into registers as soon as slice s is
+  // staged, so the loads complete under slice s's four MMA stages.
+  const int bn = tid >> 2, bxq = (tid & 3) * 4;     // this thread's B1 entries
+  const int mxo = tid >> 1, mdq = (tid & 1) * 4;    // its B4 entries (tid < 32)
+  auto load_slice = [&](int s, float (&e)[4], float (&md)[4]) {
+    const float* src = Ein + s * (Dc * 64) + bn;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) e[j] = src[(bxq + j) * 64];
     if (tid < 32) {
-      const int xo = tid >> 1, dq = (tid & 1) * 4;
-      float v[4];
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
-        const int d = dq + j;
-        v[j] = tc::to_tf32(right ? Md[xo * D * Dc + d * Dc + s] : Md[s * D * Dc + d * Dc + xo]);
+        const int d = mdq + j;
+        md[j] = right ? Md[mxo * D * Dc + d * Dc + s] : Md[s * D * Dc + d * Dc + mxo];
       }
-      st4(B4 + tc::kmaj(xo, dq, 8), v[0], v[1], v[2], v[3]);
     }
+  };
+  float pe[4], pm[4] = {0.f, 0.f, 0.f, 0.f};
+  load_slice(0, pe, pm);
+  for (int s = 0; s < Dc; ++s) {
+    // ---- B1 = Ein slice as [n = (y1i, y2i)][k = xi]; B4 = Md slice as [x'o][d2]
+    st4(B1 + tc::kmaj(bn, bxq, 16), tc::to_tf32(pe[0]), tc::to_tf32(pe[1]), tc::to_tf32(pe[2]),
+        tc::to_tf32(pe[3]));
+    if (tid < 32)
+      st4(B4 + tc::kmaj(mxo, mdq, 8), tc::to_tf32(pm[0]), tc::to_tf32(pm[1]), tc::to_tf32(pm[2]),
+          tc::to_tf32(pm[3]));
+    if (s + 1 < Dc) load_slice(s + 1, pe, pm);
     tc::fence_async_smem();
     tc::tc_fence_before();
     __syncthreads();
