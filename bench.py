@@ -257,7 +257,8 @@ def run_ours(args, rank, world, local_rank):
                    "configs_per_step_per_gpu": n,
                    "precision_path": {"fp32": "plain FP32 SIMT", "fp64": "plain FP64 SIMT",
                                       "mixed_tf32": "two-row transfers on tcgen05 (TF32 in, FP32 accumulate), "
-                                                    "rest FP32 SIMT"}[args.prec],
+                                                    "rest FP32 SIMT" if (D, Dc) == (8, 16) else
+                                                    "FP32 SIMT (the tcgen05 two-row step covers D=8, Dc=16)"}[args.prec],
                    "sampling": "uniform random Sz=0 configurations",
                    "l2": "working set per step (environments, Delta) is tens of GB, far above L2",
                    "parallelism": f"dp{world} (independent configurations)"},

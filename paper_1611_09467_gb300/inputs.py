@@ -183,21 +183,26 @@ def random_sz0(n: int, N: int, seed: int, first: int = 0) -> np.ndarray:
 
 # ---------------------------------------------------------------- workloads
 # The synthetic workloads, shaped like the paper's lattices (square lattices
-# up to 16x16, D up to 10, Dc = 2D, J1 = 1, J2/J1 in {0, 0.5}).
+# up to 16x16, D up to 10, Dc = 2D, J1 = 1, J2/J1 in {0, 0.5}).  All draw
+# their configurations uniformly in the S^z = 0 sector; Metropolis draws
+# (peps_mc_sweep) would change which configurations are evaluated, not the
+# work per configuration.
 WORKLOADS = {
     "4x4_D2_Dc4": dict(L=4, D=2, Dc=4, J2=0.5, n=64, bias=False, cfg=1,
                        sampling="uniform"),
     "8x8_D4_Dc8": dict(L=8, D=4, Dc=8, J2=0.5, n=4096, bias=True, cfg=2,
                        sampling="uniform"),
     "10x10_D6_Dc12": dict(L=10, D=6, Dc=12, J2=0.5, n=8192, bias=False, cfg=3,
-                          sampling="metropolis10"),
+                          sampling="uniform"),
     "16x16_D8_Dc16": dict(L=16, D=8, Dc=16, J2=0.5, n=16384, bias=False, cfg=4,
-                          sampling="metropolis10"),
+                          sampling="uniform"),
     "16x16_D10_Dc20": dict(L=16, D=10, Dc=20, J2=0.5, n=16384, bias=False, cfg=4,
-                           sampling="metropolis10"),
+                           sampling="uniform"),
     # the same shapes with near-product tensors: for accuracy checks at full size
     "16x16_D8_Dc16_np": dict(L=16, D=8, Dc=16, J2=0.5, n=16384, bias=False, cfg=5,
                              sampling="uniform", tensors="near_product"),
+    "16x16_D10_Dc20_np": dict(L=16, D=10, Dc=20, J2=0.5, n=16384, bias=False, cfg=6,
+                              sampling="uniform", tensors="near_product"),
 }
 
 

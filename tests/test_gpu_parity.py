@@ -60,6 +60,7 @@ CASES_FP64 = [
     (6, 5, 4, 8, 0.5, 6, True, 81),            # fused two-row step (D=4, Dc=8), truncated
     (4, 4, 8, 16, 0.5, 4, False, 82),          # D=8: cut blocks of up to 128 x 128, fused row step
     (5, 6, 6, 12, 0.5, 4, True, 83),           # D=6: cut blocks of up to 72 rows
+    (4, 4, 10, 20, 0.5, 3, False, 84),         # D=10: cut blocks of 200 rows held in global memory
 ]
 
 
@@ -163,6 +164,39 @@ def test_fp32_parity_8x8():
     cos = gg @ gref.ravel() / (np.linalg.norm(gg) * np.linalg.norm(gref))
     assert cos > 0.999, cos
     p.close()
+
+
+def test_fp32_parity_d10():
+    """D = 10, Dc = 20 (the larger 16x16 workload's shapes) on a 4x5 lattice:
+    cut blocks of 200 x 200 held in global memory, the generic single- and
+    two-row steps.  Both precision settings run FP32 here (the tensor-core
+    step covers D = 8, Dc = 16 only).  Bounds as in the 8x8 FP32 test."""
+    Ly, Lx, D, Dc, J2 = 4, 5, 10, 20, 0.5
+    A = inputs.make_tensors(Ly, Lx, D, 85)
+    spins = inputs.random_sz0(6, Ly * Lx, 85)
+    evs = oracle_evals(A, spins, Ly, Lx, Dc, J2)
+    sens = [fp32_sensitivity(A, spins[k], Ly, Lx, Dc, J2, seed=k) for k in range(len(spins))]
+    for prec in ("fp32", "mixed_tf32"):
+        p = make(A, Lx, Ly, D, Dc, J2, prec)
+        r = p.evaluate(packed(spins), logabs=True, eloc=True, O=True)
+        torch.cuda.synchronize()
+        la = r["logabs"].cpu().numpy()
+        el = r["eloc"].cpu().numpy()
+        sg = r["sign"].cpu().numpy()
+        Og = r["O"].cpu().numpy()
+        assert (r["status"].cpu().numpy() == 0).all(), prec
+        for k, ev in enumerate(evs):
+            sl, se = sens[k]
+            scale = eloc_scale(ev, Ly, Lx, 1.0, J2, spins[k])
+            print(prec, k, "dlogpsi %.2e (sens %.2e)  dE %.2e (sens %.2e, scale %.1f)"
+                  % (abs(la[k] - ev.logabs), sl, abs(el[k] - ev.eloc), se, scale))
+            assert sg[k] == ev.sign, (prec, k)
+            assert abs(la[k] - ev.logabs) < 1e-5 + FP32_COND * sl, (prec, k)
+            assert abs(el[k] - ev.eloc) < 2e-3 * scale + FP32_COND * se, (prec, k)
+            ref = ev.O.reshape(Ly * Lx, -1)
+            cos = (Og[k].ravel() @ ref.ravel()) / (np.linalg.norm(Og[k]) * np.linalg.norm(ref))
+            assert cos > 0.9999, (prec, k, cos)
+        p.close()
 
 
 def test_mixed_tf32_parity():
