@@ -284,10 +284,11 @@ def run_ours(args, rank, world, local_rank):
     return res
 
 
-# (L, D, Dc, J2/J1, precision): square lattices 6..12, D in {4, 6, 8}, Dc = 2D,
-# J2/J1 in {0, 0.5}; the D = 8 models take the tensor-core path.
+# (L, D, Dc, J2/J1, precision): square lattices 6..16, D in {4, 6, 8, 10},
+# Dc = 2D, J2/J1 in {0, 0.5}; the D = 8 models take the tensor-core path.
 SERVE_MIX = [(6, 4, 8, 0.0, "fp32"), (6, 4, 8, 0.5, "fp32"), (8, 4, 8, 0.5, "fp32"), (8, 6, 12, 0.0, "fp32"),
-             (10, 6, 12, 0.5, "fp32"), (8, 8, 16, 0.0, "mixed_tf32"), (12, 8, 16, 0.5, "mixed_tf32")]
+             (10, 6, 12, 0.5, "fp32"), (8, 8, 16, 0.0, "mixed_tf32"), (12, 8, 16, 0.5, "mixed_tf32"),
+             (16, 8, 16, 0.5, "mixed_tf32"), (6, 10, 20, 0.0, "fp32")]
 
 
 def run_serving(args):
