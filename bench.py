@@ -99,6 +99,31 @@ def cpu_oracle_rate(name, seconds):
                        f"{cores} spawned single-threaded workers, {wall:.1f} s (probe {t_probe:.1f} s)")
 
 
+# ------------------------------------------------------------ ranks (weak scaling)
+
+def rank_configurations(workload, n, rank):
+    """Rank `rank`'s own batch: configurations rank*n .. rank*n + n - 1 of the
+    workload's keyed stream.  Ranks never share a configuration, and a rank's
+    batch does not depend on the world size."""
+    w = inputs.WORKLOADS[workload]
+    return inputs.random_sz0(n, w["L"] * w["L"], inputs.SEED_BASE + w["cfg"], first=rank * n)
+
+
+def max_over_ranks(x, world, device):
+    """The largest x over the ranks (a time: the job ends with its slowest rank)."""
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(n_per_rank, world, steps, ms):
+    """Configurations per second of the whole job: every rank's batch, every
+    timed step, over the max-over-ranks time `ms`."""
+    return n_per_rank * world * steps / (ms / 1e3)
+
+
 # ------------------------------------------------------------- clock sampler
 
 def start_clock_sampler(path):
@@ -147,7 +172,7 @@ def run_ours(args, rank, world, local_rank):
     n = args.n or w["n"]
     A, _ = inputs.workload_inputs(args.workload, n=1)
     # each rank draws its own configurations (weak scaling)
-    spins = inputs.random_sz0(n, L * L, inputs.SEED_BASE + w["cfg"], first=rank * n)
+    spins = rank_configurations(args.workload, n, rank)
     S_host = torch.from_numpy(inputs.pack_spins(spins).view(np.int64)).pin_memory()
     S = S_host.cuda()
     p = PEPS(A, L, L, D, Dc, J1=1.0, J2=J2, prec=args.prec)
@@ -190,10 +215,7 @@ def run_ours(args, rank, world, local_rank):
     per_step = [x.elapsed_time(y) for x, y in step_ms]
     prof = p.profile_read(reset=True)
     p.profile(False)
-    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, world, "cuda")
     clocks = read_clocks(clk_path, local_rank)
 
     # end to end through the public API with host buffers
@@ -213,11 +235,8 @@ def run_ours(args, rank, world, local_rank):
         t1.record(stream)
         torch.cuda.synchronize()
         e_ms = t0.elapsed_time(t1)
-        te = torch.tensor([e_ms], dtype=torch.float64, device="cuda")
-        if world > 1:
-            torch.distributed.all_reduce(te, op=torch.distributed.ReduceOp.MAX)
-        e_ms = float(te.item())
-        e2e = {"value": n * world * args.steps / (e_ms / 1e3), "unit": UNIT,
+        e_ms = max_over_ranks(e_ms, world, "cuda")
+        e2e = {"value": whole_job_rate(n, world, args.steps, e_ms), "unit": UNIT,
                "h2d_bytes_per_step": int(S_host.numel() * 8),
                "d2h_bytes_per_step": int(2 * n * 8 + 8)}
 
@@ -248,7 +267,7 @@ def run_ours(args, rank, world, local_rank):
                     "flops_per_config": f_cfg}
     share = {k: round(v[0] / sum(x[0] for x in kern.values()), 4) for k, v in kern.items()}
     launches = sum(v[1] for v in kern.values())
-    value = n * world * args.steps / (total_ms / 1e3)
+    value = whole_job_rate(n, world, args.steps, total_ms)
     res = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -278,8 +297,9 @@ def run_ours(args, rank, world, local_rank):
         q.gradient(S)
         c1.record(stream)
         torch.cuda.synchronize()
-        ms = c0.elapsed_time(c1)
-        res["plain_fp32"] = {"value": n * world / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "steps": 1, "warmup": 1}
+        ms = max_over_ranks(c0.elapsed_time(c1), world, "cuda")
+        res["plain_fp32"] = {"value": whole_job_rate(n, world, 1, ms), "unit": UNIT, "ms_per_step": ms, "steps": 1,
+                             "warmup": 1}
         q.close()
     return res
 
@@ -367,20 +387,22 @@ def run_serving(args):
 
 
 def run_reference(args, rank):
+    """The reference arm: the FP64 oracle as it stands, on the host cores.
+    Rank 0 alone runs it (other ranks return None and exit without work):
+    W untimed warm-up steps, then K timed ones, each a bounded sample of the
+    workload sized so that the whole run ends within a few minutes."""
     if rank != 0:
         return None
     w = inputs.WORKLOADS[args.workload]
-    rate = None
+    per_step = max(2.0, min(args.cpu_seconds, 150.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        cpu_oracle_rate(args.workload, per_step)
     t0 = time.perf_counter()
-    samples = []
-    import multiprocessing as mp  # noqa: F401
-    for _ in range(max(1, args.warmup and 0) + args.steps):
-        c = cpu_oracle_rate(args.workload, args.cpu_seconds)
-        samples.append(c)
+    samples = [cpu_oracle_rate(args.workload, per_step) for _ in range(args.steps)]
+    wall = time.perf_counter() - t0
     rate = statistics.median([c["value"] for c in samples])
     cb = dict(samples[-1])
     cb["value"] = rate
-    wall = time.perf_counter() - t0
     return {
         "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": wall * 1e3 / max(1, args.steps), "higher_is_better": True,
