@@ -102,3 +102,79 @@ def test_zip_programs(dirn, dims):
     ref = np.einsum("aib,lrio,brk->okal", Mt, Tin, C).reshape(o * k, a * l)
     got = peps.host_zip(0, D, Dc, list(dims) + list(strides), C, M, T, (o * k, a * l))
     assert np.allclose(got, ref, rtol=1e-12, atol=1e-12)
+
+
+def _params(**kw):
+    base = dict(Lx=4, Ly=4, d=2, D=2, Dc=4, J1=1.0, J2=0.5, prec=0, workspace_gb=0.0)
+    base.update(kw)
+    return peps.Params(**base)
+
+
+def _create(params, A):
+    import ctypes
+    h = ctypes.c_void_p()
+    code = peps.lib().peps_create(ctypes.byref(params), A.ctypes.data if A is not None else None, None,
+                                  ctypes.byref(h))
+    return code, h.value, peps.lib().peps_last_error().decode()
+
+
+@pytest.mark.parametrize("kw,msg", [
+    (dict(Lx=1), "Lx, Ly"), (dict(Ly=65), "Lx, Ly"), (dict(d=3), "d must be 2"),
+    (dict(D=0), "D must be"), (dict(D=17), "D must be"), (dict(Dc=0), "Dc"), (dict(Dc=33), "Dc"),
+    (dict(D=16, Dc=17), "Dc*D"), (dict(prec=3), "precision"), (dict(J2=float("nan")), "coupling"),
+])
+def test_create_rejects_invalid_parameters(kw, msg):
+    """Argument checks of peps_create run before any device call: each bad
+    parameter returns PEPS_EINVAL with a message and leaves no handle."""
+    p = _params(**kw)
+    D = min(max(p.D, 1), 16)
+    A = np.zeros((max(p.Lx, 1) * max(p.Ly, 1), 2) + (D,) * 4)
+    code, h, err = _create(p, A)
+    assert code == 1 and h is None, (code, err)
+    assert msg in err
+
+
+def test_create_rejects_invalid_tensors():
+    """Non-finite entries and non-zero entries past an open edge (bond
+    dimension one there, Eq. 1) are rejected on the host."""
+    from paper_1611_09467_gb300 import inputs
+    A = inputs.make_tensors(4, 4, 2, 7)
+    bad = A.copy()
+    bad[5, 1, 0, 1, 1, 0] = np.nan
+    code, h, err = _create(_params(), bad)
+    assert (code, h) == (1, None) and "non-finite" in err
+    bad = A.copy()
+    bad[0, 0, 1, 0, 0, 0] = 1.0          # site 0 has no left neighbour: l must be 0
+    code, h, err = _create(_params(), bad)
+    assert (code, h) == (1, None) and "open edge" in err
+    code, h, err = _create(_params(), None)
+    assert (code, h) == (1, None) and "null" in err
+
+
+def test_calls_reject_null_context_and_bad_batches():
+    import ctypes
+    L = peps.lib()
+    la = np.zeros(1)
+    assert L.peps_amplitudes(None, la.ctypes.data, 1, la.ctypes.data, la.ctypes.data, None) == 1
+    assert "null context" in L.peps_last_error().decode()
+    p = _params(Lx=1)
+    assert L.peps_amplitudes_static(ctypes.byref(p), None, None, 0, None, None, None, None) == 1
+    assert "out of range" in L.peps_last_error().decode()
+    p = _params(prec=2)
+    assert L.peps_amplitudes_static(ctypes.byref(p), None, None, 0, None, None, None, None) == 1
+    assert "precision" in L.peps_last_error().decode()
+    p = _params()
+    assert L.peps_amplitudes_static(ctypes.byref(p), None, None, -1, None, None, None, None) == 1
+    assert [L.peps_status_str(c).decode() for c in range(6)] == [
+        "PEPS_OK", "PEPS_EINVAL", "PEPS_ENOMEM", "PEPS_ECUDA", "PEPS_ETIMEOUT", "PEPS_ENUMERIC"]
+
+
+def test_create_without_a_device_fails_cleanly():
+    """With valid arguments and no GPU, peps_create reports the CUDA error
+    instead of falling back to any host path."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_1611_09467_gb300 import inputs
+    code, h, err = _create(_params(), inputs.make_tensors(4, 4, 2, 7))
+    assert code == 3 and h is None, (code, err)
