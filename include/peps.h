@@ -188,7 +188,9 @@ peps_status peps_server_submit(peps_server* server, peps_ctx* model, const uint6
 /* Retires finished requests and admits queued ones.  wait != 0 blocks until
  * at least one request finishes (or nothing is left).  Up to max finished ids
  * and their latencies (ms, submission to completion) are written; *ndone is
- * their number. */
+ * their number.  A request that could not be launched (its workspace does not
+ * fit in device memory, or a launch failed) is returned with latency -1 and
+ * its outputs are not valid; peps_last_error says why. */
 peps_status peps_server_poll(peps_server* server, int wait, long long* ids, double* latency_ms, int max, int* ndone);
 /* stats[8]: submitted, completed, queued, running, p50 and p99 latency (ms),
  * HBM in use and peak HBM (GB) of the lanes' workspaces. */

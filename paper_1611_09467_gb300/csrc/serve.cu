@@ -171,8 +171,14 @@ peps_status step(peps_server* s) {
       ++it;   // does not fit now: let a smaller queued request pass
       continue;
     }
-    const peps_status st = launch(s, *free_lane, *it);
-    if (st != PEPS_OK) return st;
+    if (launch(s, *free_lane, *it) != PEPS_OK) {
+      // The request cannot run (its workspace does not fit in device memory,
+      // or a launch failed).  It is retired as failed, with a negative
+      // latency, so that the queue keeps moving; peps_last_error holds why.
+      s->finished.emplace_back(it->id, -1.0);
+      it = s->queue.erase(it);
+      continue;
+    }
     it = s->queue.erase(it);
   }
   return PEPS_OK;

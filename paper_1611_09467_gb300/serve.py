@@ -74,10 +74,18 @@ class Server:
         nd = ctypes.c_int()
         _p.check(_lib().peps_server_poll(self.h, 1 if wait else 0, _p._ptr(ids), _p._ptr(lat), int(max_items),
                                          ctypes.byref(nd)))
-        return [(int(ids[k]), float(lat[k])) for k in range(nd.value)]
+        done = [(int(ids[k]), float(lat[k])) for k in range(nd.value)]
+        for rid, ms in done:
+            if ms < 0 and rid in self.outputs:
+                self.outputs[rid]["failed"] = _lib().peps_last_error().decode()
+        return done
 
     def result(self, rid):
-        return self.outputs.pop(rid)
+        """The outputs of a finished request; raises if it could not be launched."""
+        out = self.outputs.pop(rid)
+        if "failed" in out:
+            raise _p.PepsError(2, f"request {rid} was not run: {out['failed']}")
+        return out
 
     def drain(self):
         done = []

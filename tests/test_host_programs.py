@@ -178,3 +178,21 @@ def test_create_without_a_device_fails_cleanly():
     from paper_1611_09467_gb300 import inputs
     code, h, err = _create(_params(), inputs.make_tensors(4, 4, 2, 7))
     assert code == 3 and h is None, (code, err)
+
+
+def test_server_argument_checks():
+    """The serving calls reject bad arguments before touching the device."""
+    import ctypes
+    from paper_1611_09467_gb300 import serve
+    L = serve._lib()
+    h = ctypes.c_void_p()
+    assert L.peps_server_create(0, 1.0, ctypes.byref(h)) == 1 and h.value is None
+    assert L.peps_server_create(65, 1.0, ctypes.byref(h)) == 1
+    assert L.peps_server_create(2, 0.0, ctypes.byref(h)) == 1
+    assert "nlanes" in L.peps_last_error().decode()
+    nd = ctypes.c_int(7)
+    assert L.peps_server_poll(None, 0, None, None, 0, ctypes.byref(nd)) == 1
+    assert L.peps_server_submit(None, None, None, 1, None, None, None, None, None, None) == 1
+    assert "bad request" in L.peps_last_error().decode()
+    st = np.zeros(8)
+    assert L.peps_server_stats(None, st.ctypes.data) == 1
