@@ -19,6 +19,8 @@ projected entangled pair states", arXiv:1611.09467):
 * Sec. IV Hamiltonian: H = J1 sum_<ij> S_i.S_j + J2 sum_<<ij>> S_i.S_j, spin 1/2.
 * Sec. II gradient: dE/dA = 2<Delta E> - 2<Delta><E>, Delta = B/W, B the
   environment of site m.
+* Sec. III gradient optimisation: A(n+1) = A(n) - p dt(n) sign(dE/dA), p
+  uniform in [0, 1) per element.
 
 Readings of points the paper leaves open (each listed in the design notes):
 zip-up truncation, alternating absorption direction, ratios and Delta taken
@@ -576,6 +578,49 @@ def mc_sweep(A, spins, Ly, Lx, Dc, seed, chain, sweep):
         Trow = [T_of(r * Lx + cc, spins[r * Lx + cc]) for cc in range(Lx)]
         mps_up, _ = absorb_row(mps_up, Trow, Dc, left_to_right=(r % 2 == 0))
     return spins, accepted
+
+
+# ------------------------------------------------------- GO update (Sec. III)
+
+def _mix64_vec(z):
+    """SplitMix64 output function on a numpy uint64 array (wrapping arithmetic)."""
+    with np.errstate(over="ignore"):
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        return z ^ (z >> np.uint64(31))
+
+
+def go_uniform(seed: int, step: int, n: int) -> np.ndarray:
+    """p in [0, 1) for the n tensor elements of GO step `step`: one SplitMix64
+    draw keyed by (seed, step, element index), top 53 bits times 2^-53."""
+    gold = np.uint64(_GOLD)
+    with np.errstate(over="ignore"):
+        h = _mix64_vec(np.uint64(seed & _MASK) + gold * np.uint64(1 + step))
+        h = _mix64_vec(h + gold * (np.uint64(1) + np.arange(n, dtype=np.uint64)))
+    return (h >> np.uint64(11)).astype(np.float64) * 2.0 ** -53
+
+
+def go_step(A, grad, dt: float, seed: int, step: int):
+    """One gradient-optimisation update (Sec. III):
+
+        A_lrud^s(n+1) = A_lrud^s(n) - p * dt(n) * sign(dE/dA_lrud^s),
+
+    p uniform in [0, 1), drawn per element.  Only the sign of the derivative
+    enters.  ``grad`` is dE/dA, [N][2][D^4] or A's shape (the estimator of
+    `gradient`).  Entries whose derivative is zero do not move: padding past
+    an open edge, or blocks that no sampled configuration selects.
+    """
+    g = np.asarray(grad, dtype=np.float64).reshape(A.shape)
+    p = go_uniform(seed, step, A.size).reshape(A.shape)
+    return A - p * dt * np.sign(g)
+
+
+def go_dt(n: int, dt0: float = 0.005, dt1: float = 0.001, n_hold: int = 50, factor: float = 0.968) -> float:
+    """Step length dt(n) of the paper's 10x10 GO run (Sec. III, Fig. 4): dt0 for
+    the first n_hold steps, then dt(n+1) = factor * dt(n) down to dt1, then dt1."""
+    if n < n_hold:
+        return dt0
+    return max(dt1, dt0 * factor ** (n - n_hold + 1))
 
 
 # ------------------------------------------------- exact diagonalisation

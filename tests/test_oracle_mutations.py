@@ -10,6 +10,7 @@ import numpy as np
 import pytest
 
 import test_oracle as P
+import test_oracle_go as G
 from oracle import peps_oracle as O
 
 PINS = {
@@ -27,6 +28,8 @@ PINS = {
     "gradient": P.test_gradient_estimator_equals_energy_derivative,
     "splitmix": P.test_sampler_uniform_is_splitmix64,
     "chi2": P.test_sampler_stationary_distribution_chi_square,
+    "go_move": G.test_go_step_moves_against_the_sign_by_less_than_dt,
+    "go_descends": G.test_go_descends_the_exact_energy,
 }
 
 
@@ -124,6 +127,18 @@ def acceptance_abs_ratio(mp):
     mp.setattr(O, "sampler_uniform", lambda *a: orig(*a) ** 2)
 
 
+def go_along_the_sign(mp):
+    """GO update with the wrong sign: A + p dt sign(dE/dA)."""
+    orig = O.go_step
+    mp.setattr(O, "go_step", lambda A, grad, dt, seed, step: 2 * A - orig(A, grad, dt, seed, step))
+
+
+def go_uses_the_value(mp):
+    """GO update with the derivative's value instead of its sign."""
+    mp.setattr(O, "go_step", lambda A, grad, dt, seed, step:
+               A - O.go_uniform(seed, step, A.size).reshape(A.shape) * dt * np.reshape(grad, A.shape))
+
+
 # each planted mistake and the pins that must catch it
 EXPECTED = [
     (drop_nnn, ["bonds", "ed_2x2"]),
@@ -135,6 +150,8 @@ EXPECTED = [
     (wrong_spin_block, ["product", "H_psi", "fd", "euler", "gradient", "chi2"]),
     (gradient_without_mean_term, ["gradient"]),
     (acceptance_abs_ratio, ["splitmix", "chi2"]),
+    (go_along_the_sign, ["go_move", "go_descends"]),
+    (go_uses_the_value, ["go_move"]),
 ]
 
 
