@@ -87,6 +87,22 @@ peps_status peps_destroy(peps_ctx* ctx);
 /* Replaces the site tensors (same shapes).  Eq. 1. */
 peps_status peps_set_tensors(peps_ctx* ctx, const double* A_host);
 
+/* One gradient-optimisation update of the site tensors (Sec. III):
+ *   A(n+1) = A(n) - p * dt * sign(dE/dA),  p uniform in [0, 1) per element.
+ * p is drawn on the device: SplitMix64's output function keyed by (seed,
+ * step, element index e of [N][2][D^4]), h = mix(seed + G (1 + step)), then
+ * h = mix(h + G (1 + e)), G = 0x9E3779B97F4A7C15, p = (h >> 11) * 2^-53.
+ *   grad_dev  [N][2][D^4] FP64 device array, dE/dA (e.g. peps_gradient's grad).
+ *   dt        step length (finite, >= 0).
+ *   A_host    [N][2][D^4] FP64 host array, caller-owned: the context's current
+ *             tensors on entry, the updated ones on return.
+ * Entries past an open edge and entries with zero derivative do not move.  The
+ * context then evaluates the updated tensors (as after peps_set_tensors).
+ * Synchronises the context's stream.  Errors: PEPS_EINVAL (null pointer, bad
+ * dt), PEPS_ENOMEM / PEPS_ECUDA. */
+peps_status peps_go_step(peps_ctx* ctx, const double* grad_dev, double dt, uint64_t seed, uint64_t step,
+                         double* A_host);
+
 /* ln|psi(S)| and sign psi(S) from the top-down boundary-MPS sweep (Fig. 1d).
  * S_dev [n][ceil(N/64)]; logabs_dev [n] FP64; sign_dev [n] int8 (+1, -1, 0);
  * status_dev [n] int32 or NULL. */

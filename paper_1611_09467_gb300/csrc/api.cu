@@ -110,7 +110,7 @@ struct peps_ctx {
   bool wm_smem = false;
   DevBuf A, triv_mps, triv_t1, triv_t2, bd, tcB;   // the model: shared by clones
   peps_ctx* parent = nullptr;                        // set on clones (model buffers borrowed)
-  DevBuf env, small, O, scratch, gsum;
+  DevBuf env, small, O, scratch, gsum, go;
   int chunk = 0;  // configurations per pass
   int res_boundary = 0, res_row = 0, res_pair = 0, res_mc = 0;  // resident CTAs per kernel
   bool pair_tc = false;  // two-row step on the tensor cores (PEPS_MIXED_TF32, D = 8, Dc = 16)
@@ -604,7 +604,7 @@ peps_status peps_destroy(peps_ctx* c) {
     cudaEventDestroy(e.second.first);
     cudaEventDestroy(e.second.second);
   }
-  DevBuf* work[] = {&c->env, &c->small, &c->O, &c->scratch, &c->gsum};
+  DevBuf* work[] = {&c->env, &c->small, &c->O, &c->scratch, &c->gsum, &c->go};
   for (DevBuf* b : work) b->release();
   if (!c->parent) {
     DevBuf* model[] = {&c->tcB, &c->A, &c->triv_mps, &c->triv_t1, &c->triv_t2, &c->bd};
@@ -619,6 +619,20 @@ peps_status peps_set_tensors(peps_ctx* c, const double* A_host) {
   peps_status st = c->elem == 8 ? upload_tensors<double>(c, A_host) : upload_tensors<float>(c, A_host);
   if (st == PEPS_OK && c->pair_tc) st = setup_tc_tiles(c, A_host);
   return st;
+}
+
+peps_status peps_go_step(peps_ctx* c, const double* grad, double dt, uint64_t seed, uint64_t step, double* A_host) {
+  if (!c || !grad || !A_host) return fail(PEPS_EINVAL, "null argument");
+  if (!std::isfinite(dt) || dt < 0.0) return fail(PEPS_EINVAL, "dt must be finite and non-negative");
+  g_err.clear();
+  const size_t D4 = (size_t)c->g.D * c->g.D * c->g.D * c->g.D;
+  const size_t bytes = (size_t)c->g.N * 2 * D4 * sizeof(double);
+  PEPS_CUDA(c->go.ensure(bytes));
+  PEPS_CUDA(cudaMemcpyAsync(c->go.p, A_host, bytes, cudaMemcpyHostToDevice, c->stream));
+  PEPS_CUDA(launch_go_step((double*)c->go.p, grad, c->g, dt, seed, step, c->nsm, c->stream));
+  PEPS_CUDA(cudaMemcpyAsync(A_host, c->go.p, bytes, cudaMemcpyDeviceToHost, c->stream));
+  PEPS_CUDA(cudaStreamSynchronize(c->stream));
+  return peps_set_tensors(c, A_host);
 }
 
 peps_status peps_evaluate(peps_ctx* c, const uint64_t* S, int n, double* logabs, int8_t* sign, double* eloc, void* O,

@@ -943,6 +943,41 @@ __device__ __forceinline__ double sampler_uniform(uint64_t seed, uint64_t chain,
   return (double)(h >> 11) * 0x1.0p-53;
 }
 
+// ------------------------------------------------------------- k_go_step
+// One gradient-optimisation update of the FP64 tensors (Sec. III):
+// A <- A - p dt sign(dE/dA), p in [0, 1) per element, from the same SplitMix64
+// construction keyed by (seed, step, element index).  Entries past an open
+// edge, and entries whose derivative is zero, do not move.  (p dt) sign is
+// exact once p dt is rounded; the _rn intrinsics keep the compiler from
+// fusing, so the result is A - (p*dt)*sign evaluated in that order.
+__global__ void k_go_step(double* A, const double* grad, Geometry geo, double dt, uint64_t seed, uint64_t step) {
+  const uint64_t G = 0x9E3779B97F4A7C15ull;
+  const size_t D = (size_t)geo.D, D4 = D * D * D * D, n = (size_t)geo.N * 2 * D4;
+  const uint64_t hs = mix64(seed + G * (1ull + step));
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    const double g = grad[e];
+    if (!(g > 0.0) && !(g < 0.0)) continue;
+    const int site = (int)(e / (2 * D4));
+    const size_t w = e % D4;
+    const size_t l = w / (D * D * D), r = w / (D * D) % D, u = w / D % D, d = w % D;
+    const int row = site / geo.Lx, col = site % geo.Lx;
+    if ((col == 0 && l) || (col == geo.Lx - 1 && r) || (row == 0 && u) || (row == geo.Ly - 1 && d)) continue;
+    const uint64_t h = mix64(hs + G * (1ull + (uint64_t)e));
+    const double p = (double)(h >> 11) * 0x1.0p-53;
+    A[e] = __dsub_rn(A[e], __dmul_rn(__dmul_rn(p, dt), g > 0.0 ? 1.0 : -1.0));
+  }
+}
+
+cudaError_t launch_go_step(double* A, const double* grad, const Geometry& geo, double dt, uint64_t seed,
+                           uint64_t step, int nsm, cudaStream_t st) {
+  const size_t n = (size_t)geo.N * 2 * geo.D * geo.D * geo.D * geo.D;
+  const size_t blocks = (n + kThreads - 1) / kThreads;
+  const int grid = (int)(blocks < (size_t)nsm * 8 ? blocks : (size_t)nsm * 8);
+  if (grid < 1) return cudaSuccess;
+  k_go_step<<<grid, kThreads, 0, st>>>(A, grad, geo, dt, seed, step);
+  return cudaGetLastError();
+}
+
 // Metropolis sweeps (sampling with weight W^2, Sec. II) over nearest-neighbour
 // exchanges: horizontal bonds row by row, then vertical bonds row pair by row
 // pair.  Lower environments are rebuilt from the current S at the start of

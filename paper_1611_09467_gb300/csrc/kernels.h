@@ -88,6 +88,9 @@ cudaError_t launch_finalize(const Geometry& g, const uint64_t* S, int n, const d
                             int have_eloc, cudaStream_t st);
 cudaError_t launch_grad_finalize(int total, int n_ok_dev_unused, const double* sums, const double* sumO,
                                  const double* sumEO, double* grad, double* cov, cudaStream_t st);
+// One gradient-optimisation update (Sec. III) of the FP64 tensors A [N][2][D^4] in place.
+cudaError_t launch_go_step(double* A, const double* grad, const Geometry& geo, double dt, uint64_t seed,
+                           uint64_t step, int nsm, cudaStream_t st);
 // Records the calling thread's error message (returned by peps_last_error).
 void set_last_error(const char* msg);
 

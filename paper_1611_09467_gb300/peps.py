@@ -51,6 +51,7 @@ def lib():
         "peps_create": [ctypes.POINTER(Params), P, P, ctypes.POINTER(P)],
         "peps_destroy": [P],
         "peps_set_tensors": [P, P],
+        "peps_go_step": [P, P, d, ctypes.c_uint64, ctypes.c_uint64, P],
         "peps_amplitudes": [P, P, i, P, P, P],
         "peps_local_energy": [P, P, i, P, P],
         "peps_log_derivatives": [P, P, i, P],
@@ -157,8 +158,9 @@ class PEPS:
         self.prec = prec
         self.real = torch.float64 if prec == "fp64" else torch.float32   # mixed paths store FP32
         self.params = Params(Lx, Ly, 2, D, Dc, float(J1), float(J2), PRECISIONS[prec], float(workspace_gb))
-        A = _f64(A)
+        A = _f64(A).copy()
         assert A.shape == (self.N, 2, D, D, D, D), A.shape
+        self.A = A                                   # the FP64 tensors the context holds
         stream = torch.cuda.current_stream().cuda_stream
         h = ctypes.c_void_p()
         check(lib().peps_create(ctypes.byref(self.params), _ptr(A), ctypes.c_void_p(stream), ctypes.byref(h)))
@@ -184,7 +186,20 @@ class PEPS:
         return S
 
     def set_tensors(self, A):
-        check(lib().peps_set_tensors(self.h, _ptr(_f64(A))))
+        A = _f64(A).copy()
+        assert A.shape == self.A.shape, A.shape
+        check(lib().peps_set_tensors(self.h, _ptr(A)))
+        self.A = A
+
+    def go_step(self, grad, dt, seed, step):
+        """One gradient-optimisation update (Sec. III) with the derivative
+        ``grad`` (CUDA FP64 [N][2][D^4], e.g. ``gradient(S)["grad"]``); the
+        context then holds the new tensors.  Returns them (FP64, host)."""
+        torch = self.torch
+        g = grad.to(device="cuda", dtype=torch.float64).contiguous()
+        assert g.numel() == self.A.size, g.shape
+        check(lib().peps_go_step(self.h, _ptr(g), float(dt), int(seed), int(step), _ptr(self.A)))
+        return self.A.copy()
 
     def evaluate(self, S, logabs=True, eloc=True, O=False):
         torch = self.torch

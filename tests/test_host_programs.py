@@ -165,6 +165,8 @@ def test_calls_reject_null_context_and_bad_batches():
     assert "precision" in L.peps_last_error().decode()
     p = _params()
     assert L.peps_amplitudes_static(ctypes.byref(p), None, None, -1, None, None, None, None) == 1
+    assert L.peps_go_step(None, None, 0.001, 1, 0, None) == 1
+    assert "null argument" in L.peps_last_error().decode()
     assert [L.peps_status_str(c).decode() for c in range(6)] == [
         "PEPS_OK", "PEPS_EINVAL", "PEPS_ENOMEM", "PEPS_ECUDA", "PEPS_ETIMEOUT", "PEPS_ENUMERIC"]
 
