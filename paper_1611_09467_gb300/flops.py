@@ -139,10 +139,10 @@ def truncation_flops(m, n, K):
     return 4 * P * Q * Q - 4 * Q ** 3 // 3 + 4 * P * Q * K + 2 * K * m * n
 
 
-def boundary_flops(Lx, Ly, D, Dc):
+def boundary_flops(Lx, Ly, D, Dc, truncation=True):
     """One configuration's boundary sweeps: top-down over all rows and
     bottom-up over rows Ly-1..1 (zip-up contractions + truncations, true
-    bond dimensions)."""
+    bond dimensions; the zip-up contractions alone with truncation=False)."""
     bd = bond_dims(Lx, Ly, D, Dc)
     total = 0
     for dr in range(2):
@@ -168,7 +168,8 @@ def boundary_flops(Lx, Ly, D, Dc):
                     last = c == 0
                 if not last:
                     K = min(Dc, m, n)
-                    total += truncation_flops(m, n, K)
+                    if truncation:
+                        total += truncation_flops(m, n, K)
                     k = K
             b = list(bd[dr, j])
     return total
