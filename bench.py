@@ -21,6 +21,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -186,7 +187,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     p.profile_read(reset=True)
     p.profile(True)
-    clk_path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv")
+    clk_path = os.path.join(tempfile.gettempdir(), f"peps_bench_clocks_rank{rank}.csv")
     os.makedirs(os.path.dirname(clk_path), exist_ok=True)
     sampler, fh = start_clock_sampler(clk_path)
     if world > 1:
@@ -353,7 +354,8 @@ def run_serving(args):
     reqs = [make_request(int(rng.integers(len(models))), 20_000 + i) for i in range(len(arrivals))]
     torch.cuda.synchronize()
     srv2 = Server(nlanes=args.lanes, hbm_budget_gb=budget)
-    sampler, fh = start_clock_sampler(os.path.join(ROOT, "gpurun_out", "clocks_serve.csv"))
+    clk_serve = os.path.join(tempfile.gettempdir(), "peps_bench_clocks_serve.csv")
+    sampler, fh = start_clock_sampler(clk_serve)
     t0 = time.perf_counter()
     lat = []
     for (k, S), ta in zip(reqs, arrivals):
@@ -379,7 +381,7 @@ def run_serving(args):
                    f"(70% of the closed-loop capacity {capacity:.2f}/s)", "lanes": args.lanes, "hbm_budget_gb": budget,
                    "duration_s": args.serve_seconds},
         "server": st, "probe_ms_per_model": probe_ms,
-        "clocks": read_clocks(os.path.join(ROOT, "gpurun_out", "clocks_serve.csv"), 0),
+        "clocks": read_clocks(clk_serve, 0),
     }
     srv.close()
     srv2.close()
