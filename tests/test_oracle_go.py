@@ -82,3 +82,17 @@ def test_go_descends_the_exact_energy():
         es.append(energy(A))
     assert all(b < a for a, b in zip(es, es[1:])), es
     assert es[-1] > e0
+
+
+def test_exact_gradient_go_driver_descends():
+    """oracle/go_exact.py on 2x2 (3 steps): energies fall and stay above ED."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-m", "oracle.go_exact", "--L", "2", "--steps", "3", "--workers", "1"],
+                       cwd=root, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [x.split() for x in r.stdout.splitlines() if x and not x.startswith("#")]
+    e = [float(x[2]) for x in lines]
+    assert len(e) == 3 and e[0] > e[1] > e[2] > -0.5
