@@ -94,12 +94,16 @@ peps_status peps_set_tensors(peps_ctx* ctx, const double* A_host);
  * h = mix(h + G (1 + e)), G = 0x9E3779B97F4A7C15, p = (h >> 11) * 2^-53.
  *   grad_dev  [N][2][D^4] FP64 device array, dE/dA (e.g. peps_gradient's grad).
  *   dt        step length (finite, >= 0).
- *   A_host    [N][2][D^4] FP64 host array, caller-owned: the context's current
- *             tensors on entry, the updated ones on return.
- * Entries past an open edge and entries with zero derivative do not move.  The
- * context then evaluates the updated tensors (as after peps_set_tensors).
- * Synchronises the context's stream.  Errors: PEPS_EINVAL (null pointer, bad
- * dt), PEPS_ENOMEM / PEPS_ECUDA. */
+ *   A_host    optional [N][2][D^4] FP64 host array, caller-owned: receives the
+ *             updated tensors; NULL skips the copy.
+ * The update runs in place on the context's FP64 copy of the tensors, on the
+ * device; the FP32 and tensor-core copies are then rebuilt from it on the
+ * device, so the context evaluates the updated tensors (as after
+ * peps_set_tensors with them).  Entries past an open edge and entries with
+ * zero derivative do not move.  Synchronises the context's stream.  Errors:
+ * PEPS_EINVAL (null context or gradient, bad dt, a NaN or infinite entry in
+ * grad_dev -- the tensors are then left unchanged -- or a serving worker
+ * context), PEPS_ENOMEM / PEPS_ECUDA. */
 peps_status peps_go_step(peps_ctx* ctx, const double* grad_dev, double dt, uint64_t seed, uint64_t step,
                          double* A_host);
 

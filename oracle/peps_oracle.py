@@ -608,9 +608,14 @@ def go_step(A, grad, dt: float, seed: int, step: int):
     p uniform in [0, 1), drawn per element.  Only the sign of the derivative
     enters.  ``grad`` is dE/dA, [N][2][D^4] or A's shape (the estimator of
     `gradient`).  Entries whose derivative is zero do not move: padding past
-    an open edge, or blocks that no sampled configuration selects.
+    an open edge, or blocks that no sampled configuration selects.  A NaN or
+    infinite derivative has no sign, so such a gradient is rejected
+    (ValueError) and nothing moves.
     """
     g = np.asarray(grad, dtype=np.float64).reshape(A.shape)
+    if not np.isfinite(g).all():
+        # the rule moves an entry against the sign of its derivative; NaN has no sign
+        raise ValueError("dE/dA holds NaN or infinite entries")
     p = go_uniform(seed, step, A.size).reshape(A.shape)
     return A - p * dt * np.sign(g)
 

@@ -17,8 +17,17 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT, "libpeps.so")
-SOURCES = ["kernels.cu", "api.cu", "serve.cu"]
-HEADERS = ["contract.cuh", "device.cuh", "kernels.h", "pair_fused.cuh", "pair_tc.cuh", os.path.join("..", "..", "include", "peps.h")]
+SOURCES = ["kernels.cu", "row.cu", "pair.cu", "mc.cu", "api.cu", "serve.cu"]
+INCLUDE = os.path.join(ROOT, "include")
+
+
+def _headers():
+    """Every header the sources can include: csrc/*.cuh, csrc/*.h and include/*.h
+    (listed from the directories, so a new header cannot be left out)."""
+    out = [os.path.join(CSRC, f) for f in sorted(os.listdir(CSRC)) if f.endswith((".cuh", ".h"))]
+    if os.path.isdir(INCLUDE):
+        out += [os.path.join(INCLUDE, f) for f in sorted(os.listdir(INCLUDE)) if f.endswith(".h")]
+    return out
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
@@ -35,7 +44,7 @@ def _stale() -> bool:
     if not os.path.exists(LIB):
         return True
     t = os.path.getmtime(LIB)
-    deps = [os.path.join(CSRC, f) for f in SOURCES + HEADERS] + [os.path.abspath(__file__)]
+    deps = [os.path.join(CSRC, f) for f in SOURCES] + _headers() + [os.path.abspath(__file__)]
     return any(os.path.getmtime(d) > t for d in deps if os.path.exists(d))
 
 

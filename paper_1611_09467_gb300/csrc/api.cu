@@ -108,7 +108,7 @@ struct peps_ctx {
   int nslots = 0;
   size_t elem = 8;
   bool wm_smem = false;
-  DevBuf A, triv_mps, triv_t1, triv_t2, bd, tcB;   // the model: shared by clones
+  DevBuf A, A64, triv_mps, triv_t1, triv_t2, bd, tcB;   // the model: shared by clones
   peps_ctx* parent = nullptr;                        // set on clones (model buffers borrowed)
   DevBuf env, small, O, scratch, gsum, go;
   int chunk = 0;  // configurations per pass
@@ -146,59 +146,35 @@ struct Prof {
 
 namespace {
 
-template <typename R>
-peps_status upload_tensors(peps_ctx* c, const double* A_host) {
+// FP64 master copy of the site tensors: the context's A itself on the FP64
+// path, a separate buffer otherwise.
+double* master_tensors(peps_ctx* c) { return c->elem == 8 ? (double*)c->A.p : (double*)c->A64.p; }
+
+// The working copies derived on the device from the FP64 master: the FP32
+// tensors and, on the tensor-core path, the pre-arranged TF32 B tiles.
+peps_status refresh_working_copies(peps_ctx* c) {
   const size_t D4 = (size_t)c->g.D * c->g.D * c->g.D * c->g.D;
   const size_t nel = (size_t)c->g.N * 2 * D4;
-  std::vector<R> h(nel);
-  for (size_t i = 0; i < nel; ++i) h[i] = (R)A_host[i];
-  PEPS_CUDA(c->A.ensure(nel * sizeof(R)));
-  PEPS_CUDA(cudaMemcpyAsync(c->A.p, h.data(), nel * sizeof(R), cudaMemcpyHostToDevice, c->stream));
-  PEPS_CUDA(cudaStreamSynchronize(c->stream));
+  if (c->elem == 4) {
+    PEPS_CUDA(c->A.ensure(nel * sizeof(float)));
+    PEPS_CUDA(launch_to_f32((const double*)c->A64.p, (float*)c->A.p, nel, c->nsm, c->stream));
+  }
+  if (c->pair_tc) {
+    PEPS_CUDA(c->tcB.ensure((size_t)2 * c->g.N * 2 * 2 * kTcTile * sizeof(float)));
+    PEPS_CUDA(launch_tc_tiles(master_tensors(c), (float*)c->tcB.p, c->g.N, c->nsm, c->stream));
+  }
   return PEPS_OK;
 }
 
-// TF32 rounding to nearest, ties away from zero (the rounding of cvt.rna.tf32.f32).
-float tf32_rna(float x) {
-  uint32_t b;
-  std::memcpy(&b, &x, 4);
-  if ((b & 0x7F800000u) != 0x7F800000u) b = (b + 0x1000u) & 0xFFFFE000u;
-  float r;
-  std::memcpy(&r, &b, 4);
-  return r;
-}
-
-// Site tensors as the B tiles of the tensor-core two-row step (pair_tc.cuh):
-// per (direction, site, spin) TA[n=(yout,d)][k=(u,yin)] and TB[n=(yout,d)][k=(yin,u)],
-// core-matrix layout, TF32-rounded.
-peps_status setup_tc_tiles(peps_ctx* c, const double* A_host) {
-  const int N = c->g.N, D = 8;
-  const size_t tile = kTcTile, per = 2 * tile;
-  std::vector<float> h((size_t)2 * N * 2 * per, 0.f);
-  auto kmaj = [](int row, int k, int K) { return (row >> 3) * (K >> 2) * 32 + (k >> 2) * 32 + (row & 7) * 4 + (k & 3); };
-  for (int dir = 0; dir < 2; ++dir)
-    for (int i = 0; i < N; ++i)
-      for (int sp = 0; sp < 2; ++sp) {
-        float* TA = h.data() + ((size_t)(dir * N + i) * 2 + sp) * per;
-        float* TB = TA + tile;
-        const double* Ai = A_host + ((size_t)i * 2 + sp) * 4096;
-        for (int n = 0; n < 64; ++n)
-          for (int k = 0; k < 64; ++k) {
-            const int yout = n >> 3, d = n & 7;
-            {
-              const int u = k >> 3, yin = k & 7;
-              const int l = dir == 0 ? yin : yout, r = dir == 0 ? yout : yin;
-              TA[kmaj(n, k, 64)] = tf32_rna((float)Ai[l * 512 + r * 64 + u * D + d]);
-            }
-            {
-              const int yin = k >> 3, u = k & 7;
-              const int l = dir == 0 ? yin : yout, r = dir == 0 ? yout : yin;
-              TB[kmaj(n, k, 64)] = tf32_rna((float)Ai[l * 512 + r * 64 + u * D + d]);
-            }
-          }
-      }
-  PEPS_CUDA(c->tcB.ensure(h.size() * sizeof(float)));
-  PEPS_CUDA(cudaMemcpy(c->tcB.p, h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice));
+peps_status upload_tensors(peps_ctx* c, const double* A_host) {
+  const size_t D4 = (size_t)c->g.D * c->g.D * c->g.D * c->g.D;
+  const size_t bytes = (size_t)c->g.N * 2 * D4 * sizeof(double);
+  DevBuf& m = c->elem == 8 ? c->A : c->A64;
+  PEPS_CUDA(m.ensure(bytes));
+  PEPS_CUDA(cudaMemcpyAsync(m.p, A_host, bytes, cudaMemcpyHostToDevice, c->stream));
+  peps_status st = refresh_working_copies(c);
+  if (st != PEPS_OK) return st;
+  PEPS_CUDA(cudaStreamSynchronize(c->stream));
   return PEPS_OK;
 }
 
@@ -481,6 +457,7 @@ peps_ctx* ctx_clone(peps_ctx* c, cudaStream_t stream, double workspace_gb, int s
     dst.bytes = src.bytes;
   };
   borrow(k->A, c->A);
+  borrow(k->A64, c->A64);
   borrow(k->triv_mps, c->triv_mps);
   borrow(k->triv_t1, c->triv_t1);
   borrow(k->triv_t2, c->triv_t2);
@@ -585,9 +562,8 @@ peps_status peps_create(const peps_params* p, const double* A_host, void* stream
     c->res_mc = max_blocks_mc<float>(c->g);
   }
   c->nslots = std::max(std::max(c->res_boundary, c->res_row), std::max(c->res_pair, c->res_mc));
-  peps_status st = c->elem == 8 ? upload_tensors<double>(c, A_host) : upload_tensors<float>(c, A_host);
+  peps_status st = upload_tensors(c, A_host);
   if (st == PEPS_OK) st = c->elem == 8 ? setup_trivial<double>(c) : setup_trivial<float>(c);
-  if (st == PEPS_OK && c->pair_tc) st = setup_tc_tiles(c, A_host);
   if (st != PEPS_OK) {
     peps_destroy(c);
     return st;
@@ -607,7 +583,7 @@ peps_status peps_destroy(peps_ctx* c) {
   DevBuf* work[] = {&c->env, &c->small, &c->O, &c->scratch, &c->gsum, &c->go};
   for (DevBuf* b : work) b->release();
   if (!c->parent) {
-    DevBuf* model[] = {&c->tcB, &c->A, &c->triv_mps, &c->triv_t1, &c->triv_t2, &c->bd};
+    DevBuf* model[] = {&c->tcB, &c->A, &c->A64, &c->triv_mps, &c->triv_t1, &c->triv_t2, &c->bd};
     for (DevBuf* b : model) b->release();
   }
   delete c;
@@ -616,23 +592,31 @@ peps_status peps_destroy(peps_ctx* c) {
 
 peps_status peps_set_tensors(peps_ctx* c, const double* A_host) {
   if (!c || !A_host) return fail(PEPS_EINVAL, "null argument");
-  peps_status st = c->elem == 8 ? upload_tensors<double>(c, A_host) : upload_tensors<float>(c, A_host);
-  if (st == PEPS_OK && c->pair_tc) st = setup_tc_tiles(c, A_host);
-  return st;
+  if (c->parent) return fail(PEPS_EINVAL, "a worker context shares its model's tensors");
+  return upload_tensors(c, A_host);
 }
 
 peps_status peps_go_step(peps_ctx* c, const double* grad, double dt, uint64_t seed, uint64_t step, double* A_host) {
-  if (!c || !grad || !A_host) return fail(PEPS_EINVAL, "null argument");
+  if (!c || !grad) return fail(PEPS_EINVAL, "null argument");
+  if (c->parent) return fail(PEPS_EINVAL, "a worker context shares its model's tensors");
   if (!std::isfinite(dt) || dt < 0.0) return fail(PEPS_EINVAL, "dt must be finite and non-negative");
   g_err.clear();
   const size_t D4 = (size_t)c->g.D * c->g.D * c->g.D * c->g.D;
   const size_t bytes = (size_t)c->g.N * 2 * D4 * sizeof(double);
-  PEPS_CUDA(c->go.ensure(bytes));
-  PEPS_CUDA(cudaMemcpyAsync(c->go.p, A_host, bytes, cudaMemcpyHostToDevice, c->stream));
-  PEPS_CUDA(launch_go_step((double*)c->go.p, grad, c->g, dt, seed, step, c->nsm, c->stream));
-  PEPS_CUDA(cudaMemcpyAsync(A_host, c->go.p, bytes, cudaMemcpyDeviceToHost, c->stream));
+  // a NaN or infinite derivative has no sign to step against: reject the step
+  PEPS_CUDA(c->go.ensure(sizeof(int)));
+  PEPS_CUDA(cudaMemsetAsync(c->go.p, 0, sizeof(int), c->stream));
+  PEPS_CUDA(launch_go_check(grad, c->g, (int*)c->go.p, c->nsm, c->stream));
+  int bad = 0;
+  PEPS_CUDA(cudaMemcpyAsync(&bad, c->go.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   PEPS_CUDA(cudaStreamSynchronize(c->stream));
-  return peps_set_tensors(c, A_host);
+  if (bad) return fail(PEPS_EINVAL, "the derivative holds NaN or infinite entries; the tensors are unchanged");
+  PEPS_CUDA(launch_go_step(master_tensors(c), grad, c->g, dt, seed, step, c->nsm, c->stream));
+  peps_status st = refresh_working_copies(c);
+  if (st != PEPS_OK) return st;
+  if (A_host) PEPS_CUDA(cudaMemcpyAsync(A_host, master_tensors(c), bytes, cudaMemcpyDeviceToHost, c->stream));
+  PEPS_CUDA(cudaStreamSynchronize(c->stream));
+  return PEPS_OK;
 }
 
 peps_status peps_evaluate(peps_ctx* c, const uint64_t* S, int n, double* logabs, int8_t* sign, double* eloc, void* O,

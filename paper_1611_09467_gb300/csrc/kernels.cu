@@ -1,4 +1,7 @@
-// CUDA kernels of the PEPS sampling path (sm_103a).
+// CUDA kernels of the PEPS sampling path (sm_103a): layouts, the boundary
+// sweeps, E_loc and gradient reductions, the GO update and the
+// allocation-free amplitudes.  The sandwich kernels are in row.cu and pair.cu,
+// the Metropolis kernel in mc.cu.
 //
 //   k_boundary : boundary-MPS sweeps (Fig. 1d): top-down U_r (gives ln|psi|,
 //                sign) and bottom-up L_r, alternating zip-up with truncation
@@ -19,50 +22,11 @@
 //
 // Kernels are persistent over work items (grid-stride), so the per-CTA
 // scratch slots bound the workspace.
-#include <algorithm>
-#include <cstdio>
-#include <cstring>
 #include <mutex>
 
-#include "../../include/peps.h"
-
-#include "device.cuh"
-#include "kernels.h"
-#include "pair_fused.cuh"
-#include "row_fused.cuh"
-#include "pair_tc.cuh"
+#include "kernels_common.cuh"
 
 namespace peps {
-
-__device__ __forceinline__ int spin_of(const uint64_t* sp, int i) { return (int)((sp[i >> 6] >> (i & 63)) & 1ull); }
-
-template <typename R>
-__device__ __forceinline__ const R* tptr(const KArgs<R>& a, int site, int s) {
-  const size_t D4 = (size_t)a.g.D * a.g.D * a.g.D * a.g.D;
-  return a.A + ((size_t)site * 2 + s) * D4;
-}
-
-struct TDims {
-  int l, r, u, d;
-};
-__device__ __forceinline__ TDims tdims(const Geometry& g, int row, int col) {
-  TDims t;
-  t.l = col == 0 ? 1 : g.D;
-  t.r = col == g.Lx - 1 ? 1 : g.D;
-  t.u = row == 0 ? 1 : g.D;
-  t.d = row == g.Ly - 1 ? 1 : g.D;
-  return t;
-}
-
-// Kernels with large shared-memory footprints ask for the maximum carve-out so
-// the occupancy the grids are sized for is the one the hardware grants.
-template <typename F>
-static cudaError_t prefer_shared(F* f, size_t smem) {
-  cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
-  return e;
-}
 
 // ---------------------------------------------------------------- layouts
 size_t wm_smem_bytes(const Geometry& g, size_t elem) {
@@ -73,34 +37,12 @@ size_t wm_smem_bytes(const Geometry& g, size_t elem) {
 // Dynamic shared memory of a kernel: a region of reals followed by the GEMM
 // offset tables.  For the kernels that truncate, the reals hold (truncation
 // matrix if it fits) + the two singular-vector blocks during a truncation and
-// the GEMM tiles otherwise; the two uses are never live together.
-__host__ __device__ inline size_t trunc_smem_reals(const Geometry& g, bool wm_in_smem) {
-  const size_t P = (size_t)g.Dc * g.D;
-  return (wm_in_smem ? P * (P + 1) : 0) + 2 * P * (size_t)g.Dc;
-}
-
-__host__ __device__ inline size_t reals_region_bytes(const Geometry& g, size_t elem, bool truncates, bool wm_in_smem) {
-  size_t r = (size_t)kGemmSmemReals;
-  if (truncates) {
-    const size_t t = trunc_smem_reals(g, wm_in_smem);
-    r = r > t ? r : t;
-  }
-  return (r * elem + 15) / 16 * 16;
-}
-
 size_t dyn_smem_bytes(const Geometry& g, size_t elem, bool truncates, bool wm_in_smem) {
   return reals_region_bytes(g, elem, truncates, wm_in_smem) + (size_t)kGemmSmemInts * sizeof(int);
 }
 
 bool wm_fits_smem(const Geometry& g, size_t elem) {
   return dyn_smem_bytes(g, elem, true, true) <= 200 * 1024;
-}
-
-template <typename R>
-__device__ __forceinline__ void smem_split(unsigned char* raw, const Geometry& g, bool truncates, bool wm_in_smem,
-                                           R*& reals, int*& ints) {
-  reals = reinterpret_cast<R*>(raw);
-  ints = reinterpret_cast<int*>(raw + reals_region_bytes(g, sizeof(R), truncates, wm_in_smem));
 }
 
 static size_t zip_elems(const Geometry& g, bool wm_in_smem) {
@@ -111,11 +53,6 @@ static size_t zip_elems(const Geometry& g, bool wm_in_smem) {
 size_t boundary_slot_elems(const Geometry& g, bool wm_in_smem) {
   const size_t envT = (size_t)g.Dc * g.D * g.Dc;
   return zip_elems(g, wm_in_smem) + (size_t)g.Lx * envT;
-}
-
-__host__ __device__ inline size_t tmp_elems(const Geometry& g) {
-  const size_t Dc = g.Dc, D = g.D;
-  return Dc * Dc * D * D * D;
 }
 
 size_t row_slot_elems(const Geometry& g) {
@@ -132,148 +69,6 @@ size_t mc_slot_elems(const Geometry& g, bool wm_in_smem) {
   const size_t envT = (size_t)g.Dc * g.D * g.Dc;
   const size_t sand = row_slot_elems(g) > pair_slot_elems(g) ? row_slot_elems(g) : pair_slot_elems(g);
   return (size_t)g.Ly * g.Lx * envT + 2 * (size_t)g.Lx * envT + zip_elems(g, wm_in_smem) + sand;
-}
-
-// ------------------------------------------------------------ zip-up row
-// Absorbs row `row` (spins `sp`) into the boundary MPS `Min` (padded
-// [Lx][Dc][D][Dc], bond dims bdin), writing `Mout` (bond dims bdout).
-// dir 0: the MPS faces the row's up legs (top-down sweep); dir 1: down legs.
-// Returns ln of the norm divided out of the last tensor (Fig. 1d with the
-// per-row normalisation that keeps the log scale).
-template <typename R>
-struct ZipBufs {
-  R* C0;
-  R* C1;
-  R* Y;
-  R* X;
-  double* dred;   // >= kWarps doubles of shared memory
-  R* gsm;         // GEMM shared scratch
-  int* gism;
-  TruncWork<R> tw;
-};
-
-template <typename R>
-__device__ double absorb_row(const KArgs<R>& a, const R* Min, R* Mout, int row, int dir, bool lr, const int* bdin,
-                        const uint64_t* sp, ZipBufs<R>& zb, R* red) {
-  const Geometry& g = a.g;
-  const int D = g.D, Dc = g.Dc, Lx = g.Lx;
-  const int envT = Dc * D * Dc;
-  const int D3 = D * D * D, DD = D * D;
-  const int sl = D3, sr = DD;
-  const int si = dir == 0 ? D : 1, so = dir == 0 ? 1 : D;
-  for (int e = threadIdx.x; e < Lx * envT; e += blockDim.x) Mout[e] = R(0);
-  R* Cc = zb.C0;
-  R* Cn = zb.C1;
-  if (threadIdx.x == 0) Cc[0] = R(1);
-  __syncthreads();
-  int kcur = 1;
-  int last;
-  if (lr) {
-    for (int c = 0; c < Lx; ++c) {
-      const TDims td = tdims(g, row, c);
-      ZipDims z;
-      z.k = kcur; z.a = bdin[c]; z.b = bdin[c + 1];
-      z.i = dir == 0 ? td.u : td.d;
-      z.l = td.l; z.r = td.r;
-      z.o = dir == 0 ? td.d : td.u;
-      const R* T = tptr(a, row * Lx + c, spin_of(sp, row * Lx + c));
-      cta_gemm<R>(zip_lr_step(0, z, D, Dc, sl, sr, si, so), Cc, Min + (size_t)c * envT, zb.Y, false, zb.gsm, zb.gism);
-      cta_gemm<R>(zip_lr_step(1, z, D, Dc, sl, sr, si, so), zb.Y, T, zb.X, false, zb.gsm, zb.gism);
-      const int m = z.k * z.o, n = z.b * z.r;
-      if (c < Lx - 1) {
-        const int K = min(Dc, min(m, n));
-        cta_topk_left<R>(zb.X, m, n, K, zb.tw, Mout + (size_t)c * envT, ix2(z.o, D * Dc, Dc), ix1(1), Cn,
-                         ix1(n), ix1(1));
-        R* t = Cc; Cc = Cn; Cn = t;
-        kcur = K;
-      } else {
-        for (int e = threadIdx.x; e < m; e += blockDim.x) {
-          const int k = e / z.o, o = e % z.o;
-          Mout[(size_t)c * envT + k * D * Dc + o * Dc] = zb.X[e];
-        }
-        __syncthreads();
-      }
-    }
-    last = Lx - 1;
-  } else {
-    for (int c = Lx - 1; c >= 0; --c) {
-      const TDims td = tdims(g, row, c);
-      ZipDims z;
-      z.k = kcur; z.a = bdin[c]; z.b = bdin[c + 1];
-      z.i = dir == 0 ? td.u : td.d;
-      z.l = td.l; z.r = td.r;
-      z.o = dir == 0 ? td.d : td.u;
-      const R* T = tptr(a, row * Lx + c, spin_of(sp, row * Lx + c));
-      cta_gemm<R>(zip_rl_step(0, z, D, Dc, sl, sr, si, so), Min + (size_t)c * envT, Cc, zb.Y, false, zb.gsm, zb.gism);
-      cta_gemm<R>(zip_rl_step(1, z, D, Dc, sl, sr, si, so), zb.Y, T, zb.X, false, zb.gsm, zb.gism);
-      const int m = z.o * z.k, n = z.a * z.l;
-      if (c > 0) {
-        const int K = min(Dc, min(m, n));
-        cta_topk_left<R>(zb.X, m, n, K, zb.tw, Mout + (size_t)c * envT, ix2(z.k, Dc, 1), ix1(D * Dc), Cn,
-                         ix1(1), ix1(K));
-        R* t = Cc; Cc = Cn; Cn = t;
-        kcur = K;
-      } else {
-        for (int e = threadIdx.x; e < m; e += blockDim.x) {
-          const int o = e / z.k, k = e % z.k;
-          Mout[o * Dc + k] = zb.X[e];
-        }
-        __syncthreads();
-      }
-    }
-    last = 0;
-  }
-  // the norm is accumulated in FP64 in every precision: ln n enters ln|psi| directly
-  double ss = 0.0;
-  R* Ml = Mout + (size_t)last * envT;
-  for (int e = threadIdx.x; e < envT; e += blockDim.x) ss += (double)Ml[e] * (double)Ml[e];
-  ss = block_sum(ss, zb.dred);
-  const double nrm = sqrt(ss);
-  if (nrm > 0.0) {
-    const R inv = (R)(1.0 / nrm);
-    for (int e = threadIdx.x; e < envT; e += blockDim.x) Ml[e] *= inv;
-  }
-  __syncthreads();
-  return nrm;
-}
-
-template <typename R>
-__device__ void carve_zip(const Geometry& g, R*& p, ZipBufs<R>& zb, R* wm_smem, R* red, double* dred, R* wv,
-                          R* gsm, int* gism) {
-  zb.dred = dred;
-  zb.gsm = gsm;
-  zb.gism = gism;
-  zb.tw.wv = wv;
-  zb.tw.gsm = gsm;
-  zb.tw.gism = gism;
-  const size_t Dc = g.Dc, D = g.D, P = Dc * D;
-  zb.C0 = p; p += Dc * Dc * D;
-  zb.C1 = p; p += Dc * Dc * D;
-  zb.Y = p; p += Dc * Dc * D * D;
-  zb.X = p; p += P * P;
-  TruncWork<R>& w = zb.tw;
-  w.ldw = (int)P + 1;
-  w.Wg = p; p += P * (P + 1);
-  R* sh = gsm;   // shared reals region: [Wm][Ubs][Uks]
-  if (wm_smem) {
-    w.Wm = sh;
-    sh += P * (P + 1);
-  } else {
-    w.Wm = p; p += P * (P + 1);
-  }
-  w.Ubs = sh; sh += P * Dc;
-  w.Uks = sh;
-  w.Qmax = (int)P;
-  w.tau = p; p += 4 * P;
-  w.t = p; p += 2 * P;
-  w.t2 = p; p += 2 * P;
-  w.lam = p; p += Dc;
-  w.Z = p; p += Dc * 2 * P;
-  w.lu = p; p += Dc * 6 * 2 * P;
-  w.Ub = p; p += P * Dc;
-  w.Uk = p; p += P * Dc;
-  p += 64;
-  w.red = red;
 }
 
 // ------------------------------------------------------------ k_boundary
@@ -348,480 +143,6 @@ __global__ void __launch_bounds__(kThreads) k_boundary(KArgs<R> a, int dirs) {
       atomicOr(&a.flags[cfg], kFlagZeroW);
     }
   }
-}
-
-template <typename R>
-__device__ R block_dot(const R* x, const R* y, int n, R* red) {
-  R s = R(0);
-  for (int e = threadIdx.x; e < n; e += blockDim.x) s += x[e] * y[e];
-  return block_sum(s, red);
-}
-
-// ----------------------------------------------------------------- k_row
-template <typename R>
-__global__ void __launch_bounds__(kThreads) k_row(KArgs<R> a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ R red[64];
-  __shared__ uint64_t sp[kMaxWords];
-  const Geometry& g = a.g;
-  const int Lx = g.Lx, Ly = g.Ly, Dc = g.Dc, D = g.D;
-  const int envT = Dc * D * Dc, D4 = D * D * D * D;
-  R* gsm;
-  int* gism;
-  smem_split<R>(smem_raw, g, false, false, gsm, gism);
-  R* p = a.scratch + (size_t)blockIdx.x * a.slot_elems;
-  R* Gb = p; p += (size_t)(Lx + 1) * envT;
-  R* F0 = p; p += envT;
-  R* F1 = p; p += envT;
-  R* X1 = p; p += envT;
-  R* X2 = p; p += envT;
-  R* Bb = p; p += D4;
-  R* t0 = p; p += tmp_elems(g);
-  R* t1 = p;
-  __shared__ int eG[kMaxL + 1];   // G_c is stored scaled by 2^-eG[c]
-  for (int item = blockIdx.x; item < a.n * Ly; item += gridDim.x) {
-    const int cfg = item / Ly, r = item % Ly;
-    __syncthreads();
-    for (int i = threadIdx.x; i < g.nwords; i += blockDim.x) sp[i] = a.S[(size_t)cfg * g.nwords + i];
-    for (int e = threadIdx.x; e < envT; e += blockDim.x) Gb[(size_t)Lx * envT + e] = a.triv_t1[e];
-    if (threadIdx.x == 0) eG[Lx] = 0;
-    __syncthreads();
-    const R* Mu = r == 0 ? a.triv_mps : a.envU + ((size_t)cfg * Ly + (r - 1)) * Lx * envT;
-    const R* Md = r == Ly - 1 ? a.triv_mps : a.envL + ((size_t)cfg * Ly + (r + 1)) * Lx * envT;
-    int eacc = 0;
-    for (int c = Lx - 1; c >= 0; --c) {
-      const int site = r * Lx + c;
-      run_op<R>(OP_COL1_RIGHT, D, Dc, Gb + (size_t)(c + 1) * envT, Mu + (size_t)c * envT,
-                tptr(a, site, spin_of(sp, site)), Md + (size_t)c * envT, nullptr, Gb + (size_t)c * envT, t0, t1, gsm, gism);
-      eacc += normalize_pow2(Gb + (size_t)c * envT, envT, red);
-      if (threadIdx.x == 0) eG[c] = eacc;
-    }
-    const R W = Gb[0];
-    const bool ok = W != R(0);
-    double eh = 0.0;
-    const R* F = a.triv_t1;
-    int eF = 0;   // F is stored scaled by 2^-eF
-    R* Fn = F0;
-    for (int c = 0; c < Lx; ++c) {
-      const int site = r * Lx + c;
-      const int s = spin_of(sp, site);
-      if (a.O != nullptr) {
-        run_op<R>(OP_SITE_ENV, D, Dc, F, Mu + (size_t)c * envT, Md + (size_t)c * envT,
-                  Gb + (size_t)(c + 1) * envT, nullptr, Bb, t0, t1, gsm, gism);
-        R* Oo = a.O + ((size_t)cfg * g.N + site) * D4;
-        const R inv = ok ? (R)ldexp(1.0 / (double)W, eF + eG[c + 1] - eG[0]) : R(0);
-        for (int e = threadIdx.x; e < D4; e += blockDim.x) Oo[e] = Bb[e] * inv;
-      }
-      if (c < Lx - 1) {
-        const int s2 = spin_of(sp, site + 1);
-        if (s != s2) {
-          run_op<R>(OP_COL1_LEFT, D, Dc, F, Mu + (size_t)c * envT, tptr(a, site, s2), Md + (size_t)c * envT,
-                    nullptr, X1, t0, t1, gsm, gism);
-          const int eX = normalize_pow2(X1, envT, red);
-          run_op<R>(OP_COL1_LEFT, D, Dc, X1, Mu + (size_t)(c + 1) * envT, tptr(a, site + 1, s),
-                    Md + (size_t)(c + 1) * envT, nullptr, X2, t0, t1, gsm, gism);
-          const R wp = block_dot(X2, Gb + (size_t)(c + 2) * envT, envT, red);
-          if (ok) eh += 0.5 * g.J1 * ldexp((double)wp / (double)W, eF + eX + eG[c + 2] - eG[0]);
-        }
-        run_op<R>(OP_COL1_LEFT, D, Dc, F, Mu + (size_t)c * envT, tptr(a, site, s), Md + (size_t)c * envT,
-                  nullptr, Fn, t0, t1, gsm, gism);
-        eF += normalize_pow2(Fn, envT, red);
-        F = Fn;
-        Fn = (Fn == F0) ? F1 : F0;
-      }
-    }
-    if (threadIdx.x == 0) {
-      a.eloc_h[(size_t)cfg * Ly + r] = eh;
-      a.w_row[(size_t)cfg * Ly + r] = (double)W;
-      if (!ok) atomicOr(&a.flags[cfg], kFlagZeroW);
-    }
-  }
-}
-
-// ------------------------------------------------------------- k_row_fused
-// k_row with the fused shared-memory step and site environment
-// (row_fused.cuh) for a fixed (D, Dc).  Transfers are stored [x'][x][y].
-template <typename R, int D, int Dc>
-__global__ void __launch_bounds__(kThreads) k_row_fused(KArgs<R> a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ R red[64];
-  __shared__ uint64_t sp[kMaxWords];
-  R* sm = reinterpret_cast<R*>(smem_raw);
-  const Geometry& g = a.g;
-  const int Lx = g.Lx, Ly = g.Ly;
-  constexpr int envT = Dc * D * Dc, D4 = D * D * D * D;
-  R* p = a.scratch + (size_t)blockIdx.x * a.slot_elems;
-  R* Gb = p; p += (size_t)(Lx + 1) * envT;
-  R* F0 = p; p += envT;
-  R* F1 = p; p += envT;
-  R* X1 = p;
-  __shared__ int eG[kMaxL + 1];   // G_c is stored scaled by 2^-eG[c]
-  for (int item = blockIdx.x; item < a.n * Ly; item += gridDim.x) {
-    const int cfg = item / Ly, r = item % Ly;
-    __syncthreads();
-    for (int i = threadIdx.x; i < g.nwords; i += blockDim.x) sp[i] = a.S[(size_t)cfg * g.nwords + i];
-    for (int e = threadIdx.x; e < envT; e += blockDim.x) Gb[(size_t)Lx * envT + e] = a.triv_t1[e];
-    if (threadIdx.x == 0) eG[Lx] = 0;
-    __syncthreads();
-    const R* Mu = r == 0 ? a.triv_mps : a.envU + ((size_t)cfg * Ly + (r - 1)) * Lx * envT;
-    const R* Md = r == Ly - 1 ? a.triv_mps : a.envL + ((size_t)cfg * Ly + (r + 1)) * Lx * envT;
-    int eacc = 0;
-    for (int c = Lx - 1; c >= 0; --c) {
-      const int site = r * Lx + c;
-      int e = 0;
-      row_step_fused<R, D, Dc>(true, Gb + (size_t)(c + 1) * envT, Gb + (size_t)c * envT, Mu + (size_t)c * envT,
-                               tptr(a, site, spin_of(sp, site)), Md + (size_t)c * envT, nullptr, sm, red, &e);
-      eacc += e;
-      if (threadIdx.x == 0) eG[c] = eacc;
-    }
-    const R W = Gb[0];
-    const bool ok = W != R(0);
-    double eh = 0.0;
-    const R* F = a.triv_t1;
-    int eF = 0;   // F is stored scaled by 2^-eF
-    R* Fn = F0;
-    for (int c = 0; c < Lx; ++c) {
-      const int site = r * Lx + c;
-      const int s = spin_of(sp, site);
-      const R* Muc = Mu + (size_t)c * envT;
-      const R* Mdc = Md + (size_t)c * envT;
-      if (a.O != nullptr)
-        site_env_fused<R, D, Dc>(F, Muc, Mdc, Gb + (size_t)(c + 1) * envT,
-                                 ok ? (R)ldexp(1.0 / (double)W, eF + eG[c + 1] - eG[0]) : R(0),
-                                 a.O + ((size_t)cfg * g.N + site) * D4, sm);
-      if (c < Lx - 1) {
-        const int s2 = spin_of(sp, site + 1);
-        if (s != s2) {
-          int eX = 0;
-          row_step_fused<R, D, Dc>(false, F, X1, Muc, tptr(a, site, s2), Mdc, nullptr, sm, red, &eX);
-          const R wp = row_step_fused<R, D, Dc>(false, X1, nullptr, Mu + (size_t)(c + 1) * envT, tptr(a, site + 1, s),
-                                                Md + (size_t)(c + 1) * envT, Gb + (size_t)(c + 2) * envT, sm, red);
-          if (ok) eh += 0.5 * g.J1 * ldexp((double)wp / (double)W, eF + eX + eG[c + 2] - eG[0]);
-        }
-        int e1 = 0;
-        row_step_fused<R, D, Dc>(false, F, Fn, Muc, tptr(a, site, s), Mdc, nullptr, sm, red, &e1);
-        eF += e1;
-        F = Fn;
-        Fn = (Fn == F0) ? F1 : F0;
-      }
-    }
-    if (threadIdx.x == 0) {
-      a.eloc_h[(size_t)cfg * Ly + r] = eh;
-      a.w_row[(size_t)cfg * Ly + r] = (double)W;
-      if (!ok) atomicOr(&a.flags[cfg], kFlagZeroW);
-    }
-  }
-}
-
-// ---------------------------------------------------------------- k_pair
-template <typename R>
-__global__ void __launch_bounds__(kThreads) k_pair(KArgs<R> a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ R red[64];
-  __shared__ uint64_t sp[kMaxWords];
-  const Geometry& g = a.g;
-  const int Lx = g.Lx, Ly = g.Ly, Dc = g.Dc, D = g.D;
-  const int envT = Dc * D * Dc, envT2 = Dc * D * D * Dc;
-  R* gsm;
-  int* gism;
-  smem_split<R>(smem_raw, g, false, false, gsm, gism);
-  R* p = a.scratch + (size_t)blockIdx.x * a.slot_elems;
-  R* Hb = p; p += (size_t)(Lx + 1) * envT2;
-  R* E0 = p; p += envT2;
-  R* E1 = p; p += envT2;
-  R* X1 = p; p += envT2;
-  R* X2 = p; p += envT2;
-  R* t0 = p; p += tmp_elems(g);
-  R* t1 = p;
-  const int npairs = Ly - 1;
-  __shared__ int eH[kMaxL + 1];   // H_c is stored scaled by 2^-eH[c]
-  for (int item = blockIdx.x; item < a.n * npairs; item += gridDim.x) {
-    const int cfg = item / npairs, r = item % npairs;
-    __syncthreads();
-    for (int i = threadIdx.x; i < g.nwords; i += blockDim.x) sp[i] = a.S[(size_t)cfg * g.nwords + i];
-    for (int e = threadIdx.x; e < envT2; e += blockDim.x) Hb[(size_t)Lx * envT2 + e] = a.triv_t2[e];
-    if (threadIdx.x == 0) eH[Lx] = 0;
-    __syncthreads();
-    const R* Mu = r == 0 ? a.triv_mps : a.envU + ((size_t)cfg * Ly + (r - 1)) * Lx * envT;
-    const R* Md = r + 2 > Ly - 1 ? a.triv_mps : a.envL + ((size_t)cfg * Ly + (r + 2)) * Lx * envT;
-    int eacc = 0;
-    for (int c = Lx - 1; c >= 0; --c) {
-      const int s1 = r * Lx + c, s2 = (r + 1) * Lx + c;
-      run_op<R>(OP_COL2_RIGHT, D, Dc, Hb + (size_t)(c + 1) * envT2, Mu + (size_t)c * envT,
-                tptr(a, s1, spin_of(sp, s1)), tptr(a, s2, spin_of(sp, s2)), Md + (size_t)c * envT,
-                Hb + (size_t)c * envT2, t0, t1, gsm, gism);
-      eacc += normalize_pow2(Hb + (size_t)c * envT2, envT2, red);
-      if (threadIdx.x == 0) eH[c] = eacc;
-    }
-    const R W = Hb[0];
-    const bool ok = W != R(0);
-    double ev = 0.0;
-    const R* E = a.triv_t2;
-    int eE = 0;   // E is stored scaled by 2^-eE
-    R* En = E0;
-    for (int c = 0; c < Lx; ++c) {
-      const int i1 = r * Lx + c, i2 = (r + 1) * Lx + c;
-      const int a1 = spin_of(sp, i1), a2 = spin_of(sp, i2);
-      const R* Muc = Mu + (size_t)c * envT;
-      const R* Mdc = Md + (size_t)c * envT;
-      if (a1 != a2) {  // vertical pair (r,c)-(r+1,c)
-        run_op<R>(OP_COL2_LEFT, D, Dc, E, Muc, tptr(a, i1, a2), tptr(a, i2, a1), Mdc, X1, t0, t1, gsm, gism);
-        const R wp = block_dot(X1, Hb + (size_t)(c + 1) * envT2, envT2, red);
-        if (ok) ev += 0.5 * g.J1 * ldexp((double)wp / (double)W, eE + eH[c + 1] - eH[0]);
-      }
-      if (c < Lx - 1 && g.J2 != 0.0) {
-        const int j1 = i1 + 1, j2 = i2 + 1;
-        const int b1 = spin_of(sp, j1), b2 = spin_of(sp, j2);
-        const R* Mun = Mu + (size_t)(c + 1) * envT;
-        const R* Mdn = Md + (size_t)(c + 1) * envT;
-        if (a1 != b2) {  // diagonal (r,c)-(r+1,c+1)
-          run_op<R>(OP_COL2_LEFT, D, Dc, E, Muc, tptr(a, i1, b2), tptr(a, i2, a2), Mdc, X1, t0, t1, gsm, gism);
-          const int eX = normalize_pow2(X1, envT2, red);
-          run_op<R>(OP_COL2_LEFT, D, Dc, X1, Mun, tptr(a, j1, b1), tptr(a, j2, a1), Mdn, X2, t0, t1, gsm, gism);
-          const R wp = block_dot(X2, Hb + (size_t)(c + 2) * envT2, envT2, red);
-          if (ok) ev += 0.5 * g.J2 * ldexp((double)wp / (double)W, eE + eX + eH[c + 2] - eH[0]);
-        }
-        if (b1 != a2) {  // anti-diagonal (r,c+1)-(r+1,c)
-          run_op<R>(OP_COL2_LEFT, D, Dc, E, Muc, tptr(a, i1, a1), tptr(a, i2, b1), Mdc, X1, t0, t1, gsm, gism);
-          const int eX = normalize_pow2(X1, envT2, red);
-          run_op<R>(OP_COL2_LEFT, D, Dc, X1, Mun, tptr(a, j1, a2), tptr(a, j2, b2), Mdn, X2, t0, t1, gsm, gism);
-          const R wp = block_dot(X2, Hb + (size_t)(c + 2) * envT2, envT2, red);
-          if (ok) ev += 0.5 * g.J2 * ldexp((double)wp / (double)W, eE + eX + eH[c + 2] - eH[0]);
-        }
-      }
-      if (c < Lx - 1) {
-        run_op<R>(OP_COL2_LEFT, D, Dc, E, Muc, tptr(a, i1, a1), tptr(a, i2, a2), Mdc, En, t0, t1, gsm, gism);
-        eE += normalize_pow2(En, envT2, red);
-        E = En;
-        En = (En == E0) ? E1 : E0;
-      }
-    }
-    if (threadIdx.x == 0) {
-      a.eloc_v[(size_t)cfg * Ly + r] = ev;
-      if (!ok) atomicOr(&a.flags[cfg], kFlagZeroW);
-    }
-  }
-}
-
-// ------------------------------------------------------------ k_pair_fused
-// k_pair with the fused shared-memory transfer step (pair_fused.cuh) for a
-// fixed (D, Dc).  Transfers are stored [x'][x][y1][y2] (see pair_fused.cuh).
-template <typename R, int D, int Dc>
-__global__ void __launch_bounds__(kThreads) k_pair_fused(KArgs<R> a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ R red[64];
-  __shared__ uint64_t sp[kMaxWords];
-  R* sm = reinterpret_cast<R*>(smem_raw);
-  const Geometry& g = a.g;
-  const int Lx = g.Lx, Ly = g.Ly;
-  constexpr int envT = Dc * D * Dc, envT2 = Dc * D * D * Dc;
-  R* p = a.scratch + (size_t)blockIdx.x * a.slot_elems;
-  R* Hb = p; p += (size_t)(Lx + 1) * envT2;
-  R* E0 = p; p += envT2;
-  R* E1 = p; p += envT2;
-  R* X1 = p;
-  const int npairs = Ly - 1;
-  __shared__ int eH[kMaxL + 1];   // H_c is stored scaled by 2^-eH[c]
-  for (int item = blockIdx.x; item < a.n * npairs; item += gridDim.x) {
-    const int cfg = item / npairs, r = item % npairs;
-    __syncthreads();
-    for (int i = threadIdx.x; i < g.nwords; i += blockDim.x) sp[i] = a.S[(size_t)cfg * g.nwords + i];
-    for (int e = threadIdx.x; e < envT2; e += blockDim.x) Hb[(size_t)Lx * envT2 + e] = a.triv_t2[e];
-    if (threadIdx.x == 0) eH[Lx] = 0;
-    __syncthreads();
-    const R* Mu = r == 0 ? a.triv_mps : a.envU + ((size_t)cfg * Ly + (r - 1)) * Lx * envT;
-    const R* Md = r + 2 > Ly - 1 ? a.triv_mps : a.envL + ((size_t)cfg * Ly + (r + 2)) * Lx * envT;
-    int eacc = 0;
-    for (int c = Lx - 1; c >= 0; --c) {
-      const int s1 = r * Lx + c, s2 = (r + 1) * Lx + c;
-      int e = 0;
-      pair_step_fused<R, D, Dc>(true, Hb + (size_t)(c + 1) * envT2, Hb + (size_t)c * envT2, Mu + (size_t)c * envT,
-                                tptr(a, s1, spin_of(sp, s1)), tptr(a, s2, spin_of(sp, s2)), Md + (size_t)c * envT,
-                                nullptr, sm, red, &e);
-      eacc += e;
-      if (threadIdx.x == 0) eH[c] = eacc;
-    }
-    const R W = Hb[0];
-    const bool ok = W != R(0);
-    double ev = 0.0;
-    const R* E = a.triv_t2;
-    int eE = 0;   // E is stored scaled by 2^-eE
-    R* En = E0;
-    for (int c = 0; c < Lx; ++c) {
-      const int i1 = r * Lx + c, i2 = (r + 1) * Lx + c;
-      const int a1 = spin_of(sp, i1), a2 = spin_of(sp, i2);
-      const R* Muc = Mu + (size_t)c * envT;
-      const R* Mdc = Md + (size_t)c * envT;
-      if (a1 != a2) {  // vertical pair (r,c)-(r+1,c)
-        const R wp = pair_step_fused<R, D, Dc>(false, E, nullptr, Muc, tptr(a, i1, a2), tptr(a, i2, a1), Mdc,
-                                               Hb + (size_t)(c + 1) * envT2, sm, red);
-        if (ok) ev += 0.5 * g.J1 * ldexp((double)wp / (double)W, eE + eH[c + 1] - eH[0]);
-      }
-      if (c < Lx - 1 && g.J2 != 0.0) {
-        const int j1 = i1 + 1, j2 = i2 + 1;
-        const int b1 = spin_of(sp, j1), b2 = spin_of(sp, j2);
-        const R* Mun = Mu + (size_t)(c + 1) * envT;
-        const R* Mdn = Md + (size_t)(c + 1) * envT;
-        if (a1 != b2) {  // diagonal (r,c)-(r+1,c+1)
-          int eX = 0;
-          pair_step_fused<R, D, Dc>(false, E, X1, Muc, tptr(a, i1, b2), tptr(a, i2, a2), Mdc, nullptr, sm, red, &eX);
-          const R wp = pair_step_fused<R, D, Dc>(false, X1, nullptr, Mun, tptr(a, j1, b1), tptr(a, j2, a1), Mdn,
-                                                 Hb + (size_t)(c + 2) * envT2, sm, red);
-          if (ok) ev += 0.5 * g.J2 * ldexp((double)wp / (double)W, eE + eX + eH[c + 2] - eH[0]);
-        }
-        if (b1 != a2) {  // anti-diagonal (r,c+1)-(r+1,c)
-          int eX = 0;
-          pair_step_fused<R, D, Dc>(false, E, X1, Muc, tptr(a, i1, a1), tptr(a, i2, b1), Mdc, nullptr, sm, red, &eX);
-          const R wp = pair_step_fused<R, D, Dc>(false, X1, nullptr, Mun, tptr(a, j1, a2), tptr(a, j2, b2), Mdn,
-                                                 Hb + (size_t)(c + 2) * envT2, sm, red);
-          if (ok) ev += 0.5 * g.J2 * ldexp((double)wp / (double)W, eE + eX + eH[c + 2] - eH[0]);
-        }
-      }
-      if (c < Lx - 1) {
-        int e1 = 0;
-        pair_step_fused<R, D, Dc>(false, E, En, Muc, tptr(a, i1, a1), tptr(a, i2, a2), Mdc, nullptr, sm, red, &e1);
-        eE += e1;
-        E = En;
-        En = (En == E0) ? E1 : E0;
-      }
-    }
-    if (threadIdx.x == 0) {
-      a.eloc_v[(size_t)cfg * Ly + r] = ev;
-      if (!ok) atomicOr(&a.flags[cfg], kFlagZeroW);
-    }
-  }
-}
-
-// ------------------------------------------------------------ k_pair_tc
-// k_pair_fused with the tensor-core step (pair_tc.cuh), D = 8, Dc = 16, TF32
-// inputs with FP32 accumulation.  Each CTA holds kTmemCols TMEM columns for
-// its lifetime; a timed-out wait marks the configuration and ends the CTA
-// after releasing TMEM.
-__global__ void __launch_bounds__(kThreads, 2) k_pair_tc(KArgs<float> a) {
-  extern __shared__ __align__(1024) unsigned char smem_raw[];
-  __shared__ float red[64];
-  __shared__ uint64_t sp[kMaxWords];
-  __shared__ __align__(8) uint64_t mbar;
-  __shared__ __align__(8) uint64_t tbar;
-  __shared__ uint32_t tmem_holder;
-  constexpr int D = 8, Dc = 16;
-  float* sm = reinterpret_cast<float*>(smem_raw);
-  const Geometry& g = a.g;
-  const int Lx = g.Lx, Ly = g.Ly;
-  constexpr int envT = Dc * D * Dc, envT2 = Dc * D * D * Dc;
-  float* p = a.scratch + (size_t)blockIdx.x * a.slot_elems;
-  float* Hb = p; p += (size_t)(Lx + 1) * envT2;
-  float* E0 = p; p += envT2;
-  float* E1 = p; p += envT2;
-  float* X1 = p;
-  if ((threadIdx.x >> 5) == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc::smem_u32(&tmem_holder)),
-                 "r"(tc::kTmemCols));
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-  }
-  if (threadIdx.x == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(tc::smem_u32(&mbar)), "r"(1));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(tc::smem_u32(&tbar)), "r"(1));
-    asm volatile("fence.mbarrier_init.release.cluster;");
-  }
-  tc::tc_fence_before();
-  __syncthreads();
-  tc::tc_fence_after();
-  PairTc st;
-  st.tmem = tmem_holder;
-  st.mbar = &mbar;
-  st.tbar = &tbar;
-  st.phase = 0;
-  st.tphase = 0;
-  st.ok = true;
-  // B tiles of site i, spin s, direction dir (0 left, 1 right): TA at +0, TB at +kTcTile
-  auto tile = [&](int dir, int i, int sp_) { return a.tcB + ((size_t)(dir * g.N + i) * 2 + sp_) * 2 * kTcTile; };
-  const int npairs = Ly - 1;
-  __shared__ int eH[kMaxL + 1];   // H_c is stored scaled by 2^-eH[c]
-  for (int item = blockIdx.x; item < a.n * npairs && st.ok; item += gridDim.x) {
-    const int cfg = item / npairs, r = item % npairs;
-    __syncthreads();
-    for (int i = threadIdx.x; i < g.nwords; i += blockDim.x) sp[i] = a.S[(size_t)cfg * g.nwords + i];
-    for (int e = threadIdx.x; e < envT2; e += blockDim.x) Hb[(size_t)Lx * envT2 + e] = a.triv_t2[e];
-    if (threadIdx.x == 0) eH[Lx] = 0;
-    __syncthreads();
-    const float* Mu = r == 0 ? a.triv_mps : a.envU + ((size_t)cfg * Ly + (r - 1)) * Lx * envT;
-    const float* Md = r + 2 > Ly - 1 ? a.triv_mps : a.envL + ((size_t)cfg * Ly + (r + 2)) * Lx * envT;
-    int eacc = 0;
-    for (int c = Lx - 1; c >= 0; --c) {
-      const int s1 = r * Lx + c, s2 = (r + 1) * Lx + c;
-      int e = 0;
-      pair_step_tc(st, true, Hb + (size_t)(c + 1) * envT2, Hb + (size_t)c * envT2, Mu + (size_t)c * envT,
-                   tile(1, s1, spin_of(sp, s1)), tile(1, s2, spin_of(sp, s2)) + kTcTile, Md + (size_t)c * envT,
-                   nullptr, sm, red, &e);
-      eacc += e;
-      if (threadIdx.x == 0) eH[c] = eacc;
-    }
-    __syncthreads();
-    const float W = Hb[0];
-    const bool ok = W != 0.f;
-    double ev = 0.0;
-    const float* E = a.triv_t2;
-    int eE = 0;   // E is stored scaled by 2^-eE
-    float* En = E0;
-    for (int c = 0; c < Lx; ++c) {
-      const int i1 = r * Lx + c, i2 = (r + 1) * Lx + c;
-      const int a1 = spin_of(sp, i1), a2 = spin_of(sp, i2);
-      const float* Muc = Mu + (size_t)c * envT;
-      const float* Mdc = Md + (size_t)c * envT;
-      if (a1 != a2) {
-        const float wp = pair_step_tc(st, false, E, nullptr, Muc, tile(0, i1, a2), tile(0, i2, a1) + kTcTile, Mdc,
-                                      Hb + (size_t)(c + 1) * envT2, sm, red);
-        if (ok) ev += 0.5 * g.J1 * ldexp((double)wp / (double)W, eE + eH[c + 1] - eH[0]);
-      }
-      if (c < Lx - 1 && g.J2 != 0.0) {
-        const int j1 = i1 + 1, j2 = i2 + 1;
-        const int b1 = spin_of(sp, j1), b2 = spin_of(sp, j2);
-        const float* Mun = Mu + (size_t)(c + 1) * envT;
-        const float* Mdn = Md + (size_t)(c + 1) * envT;
-        if (a1 != b2) {
-          int eX = 0;
-          pair_step_tc(st, false, E, X1, Muc, tile(0, i1, b2), tile(0, i2, a2) + kTcTile, Mdc, nullptr, sm, red,
-                       &eX);
-          __syncthreads();
-          const float wp = pair_step_tc(st, false, X1, nullptr, Mun, tile(0, j1, b1), tile(0, j2, a1) + kTcTile, Mdn,
-                                        Hb + (size_t)(c + 2) * envT2, sm, red);
-          if (ok) ev += 0.5 * g.J2 * ldexp((double)wp / (double)W, eE + eX + eH[c + 2] - eH[0]);
-        }
-        if (b1 != a2) {
-          int eX = 0;
-          pair_step_tc(st, false, E, X1, Muc, tile(0, i1, a1), tile(0, i2, b1) + kTcTile, Mdc, nullptr, sm, red,
-                       &eX);
-          __syncthreads();
-          const float wp = pair_step_tc(st, false, X1, nullptr, Mun, tile(0, j1, a2), tile(0, j2, b2) + kTcTile, Mdn,
-                                        Hb + (size_t)(c + 2) * envT2, sm, red);
-          if (ok) ev += 0.5 * g.J2 * ldexp((double)wp / (double)W, eE + eX + eH[c + 2] - eH[0]);
-        }
-      }
-      if (c < Lx - 1) {
-        int e1 = 0;
-        pair_step_tc(st, false, E, En, Muc, tile(0, i1, a1), tile(0, i2, a2) + kTcTile, Mdc, nullptr, sm, red, &e1);
-        __syncthreads();
-        eE += e1;
-        E = En;
-        En = (En == E0) ? E1 : E0;
-      }
-    }
-    if (threadIdx.x == 0) {
-      a.eloc_v[(size_t)cfg * Ly + r] = ev;
-      if (!ok) atomicOr(&a.flags[cfg], kFlagZeroW);
-      if (!st.ok) atomicOr(&a.flags[cfg], kFlagTimeout);
-    }
-  }
-  if (!st.ok && threadIdx.x == 0) {
-    // configurations this CTA did not reach are marked too
-    for (int item = blockIdx.x; item < a.n * npairs; item += gridDim.x) atomicOr(&a.flags[item / npairs], kFlagTimeout);
-  }
-  tc::tc_fence_before();
-  __syncthreads();
-  tc::tc_fence_after();
-  if ((threadIdx.x >> 5) == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_holder), "r"(tc::kTmemCols));
 }
 
 // ------------------------------------------------------------ k_finalize
@@ -926,23 +247,6 @@ __global__ void k_grad_finalize(int total, const double* sums, const double* sum
   }
 }
 
-// ------------------------------------------------------------------- k_mc
-// SplitMix64 output function (Steele, Lea & Flood 2014), used as a
-// counter-based generator keyed by (seed, chain, sweep, bond).
-__device__ __forceinline__ uint64_t mix64(uint64_t z) {
-  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-  return z ^ (z >> 31);
-}
-__device__ __forceinline__ double sampler_uniform(uint64_t seed, uint64_t chain, uint64_t sweep, uint64_t bond) {
-  const uint64_t G = 0x9E3779B97F4A7C15ull;
-  uint64_t h = seed;
-  h = mix64(h + G * (1ull + chain));
-  h = mix64(h + G * (1ull + sweep));
-  h = mix64(h + G * (1ull + bond));
-  return (double)(h >> 11) * 0x1.0p-53;
-}
-
 // ------------------------------------------------------------- k_go_step
 // One gradient-optimisation update of the FP64 tensors (Sec. III):
 // A <- A - p dt sign(dE/dA), p in [0, 1) per element, from the same SplitMix64
@@ -968,6 +272,65 @@ __global__ void k_go_step(double* A, const double* grad, Geometry geo, double dt
   }
 }
 
+// Sets *bad when any derivative is NaN or infinite: the update of Sec. III
+// moves an entry by the sign of its derivative, and such a derivative has none.
+__global__ void k_go_check(const double* grad, size_t n, int* bad) {
+  int b = 0;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+    if (!isfinite(grad[e])) b = 1;
+  if (__syncthreads_or(b) && threadIdx.x == 0) atomicOr(bad, 1);
+}
+
+cudaError_t launch_go_check(const double* grad, const Geometry& geo, int* bad, int nsm, cudaStream_t st) {
+  const size_t n = (size_t)geo.N * 2 * geo.D * geo.D * geo.D * geo.D;
+  const size_t blocks = (n + kThreads - 1) / kThreads;
+  const int grid = (int)(blocks < (size_t)nsm * 8 ? blocks : (size_t)nsm * 8);
+  if (grid < 1) return cudaSuccess;
+  k_go_check<<<grid, kThreads, 0, st>>>(grad, n, bad);
+  return cudaGetLastError();
+}
+
+// The context's working copy of the tensors in FP32, from the FP64 ones.
+__global__ void k_to_f32(const double* __restrict__ a, float* __restrict__ b, size_t n) {
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+    b[e] = __double2float_rn(a[e]);
+}
+
+cudaError_t launch_to_f32(const double* a, float* b, size_t n, int nsm, cudaStream_t st) {
+  const size_t blocks = (n + kThreads - 1) / kThreads;
+  const int grid = (int)(blocks < (size_t)nsm * 8 ? blocks : (size_t)nsm * 8);
+  if (grid < 1) return cudaSuccess;
+  k_to_f32<<<grid, kThreads, 0, st>>>(a, b, n);
+  return cudaGetLastError();
+}
+
+// Site tensors as the B tiles of the tensor-core two-row step (D = 8): per
+// (direction, site, spin) TA[n = (yout, d)][k = (u, yin)] and
+// TB[n = (yout, d)][k = (yin, u)] in the core-matrix layout, rounded to TF32
+// (to nearest, ties away from zero), with (yin, yout) = (l, r) for direction 0
+// and (r, l) for direction 1.  One thread per tile element.
+__global__ void k_tc_tiles(const double* __restrict__ A, float* __restrict__ tiles, int N) {
+  const size_t total = (size_t)2 * N * 2 * 2 * kTcTile;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int n = (int)(e % 4096) / 64, k = (int)(e % 64);
+    const size_t tix = e / 4096;                  // ((dir * N + i) * 2 + sp) * 2 + which
+    const int which = (int)(tix % 2), sp = (int)(tix / 2 % 2), i = (int)(tix / 4 % N), dir = (int)(tix / 4 / N);
+    const int yout = n >> 3, d = n & 7;
+    const int u = which == 0 ? (k >> 3) : (k & 7), yin = which == 0 ? (k & 7) : (k >> 3);
+    const int l = dir == 0 ? yin : yout, r = dir == 0 ? yout : yin;
+    const float v = __double2float_rn(A[((size_t)i * 2 + sp) * 4096 + l * 512 + r * 64 + u * 8 + d]);
+    uint32_t t;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(t) : "f"(v));
+    const int dst = (n >> 3) * 16 * 32 + (k >> 2) * 32 + (n & 7) * 4 + (k & 3);
+    tiles[tix * 4096 + dst] = __uint_as_float(t);
+  }
+}
+
+cudaError_t launch_tc_tiles(const double* A, float* tiles, int N, int nsm, cudaStream_t st) {
+  k_tc_tiles<<<nsm * 4, kThreads, 0, st>>>(A, tiles, N);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_go_step(double* A, const double* grad, const Geometry& geo, double dt, uint64_t seed,
                            uint64_t step, int nsm, cudaStream_t st) {
   const size_t n = (size_t)geo.N * 2 * geo.D * geo.D * geo.D * geo.D;
@@ -976,160 +339,6 @@ cudaError_t launch_go_step(double* A, const double* grad, const Geometry& geo, d
   if (grid < 1) return cudaSuccess;
   k_go_step<<<grid, kThreads, 0, st>>>(A, grad, geo, dt, seed, step);
   return cudaGetLastError();
-}
-
-// Metropolis sweeps (sampling with weight W^2, Sec. II) over nearest-neighbour
-// exchanges: horizontal bonds row by row, then vertical bonds row pair by row
-// pair.  Lower environments are rebuilt from the current S at the start of
-// each pass; the upper environment grows from the updated rows; the row (or
-// row-pair) transfers to the left are carried with the accepted spins.
-template <typename R>
-__global__ void __launch_bounds__(kThreads) k_mc(KArgs<R> a, uint64_t* S, int nsweeps, uint64_t seed, uint64_t chain0,
-                                                 uint64_t sweep0, long long* accepted) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ R red[64];
-  __shared__ uint64_t sp[kMaxWords];
-  __shared__ int ones[kMaxDcD + 1];
-  const Geometry& g = a.g;
-  const int Lx = g.Lx, Ly = g.Ly, Dc = g.Dc, D = g.D;
-  const size_t envT = (size_t)Dc * D * Dc, envT2 = envT * D;
-  R* p = a.scratch + (size_t)blockIdx.x * a.slot_elems;
-  R* envL = p; p += (size_t)Ly * Lx * envT;
-  R* Ubuf[2];
-  Ubuf[0] = p; p += (size_t)Lx * envT;
-  Ubuf[1] = p; p += (size_t)Lx * envT;
-  ZipBufs<R> zb;
-  __shared__ double dred[kWarps];
-  __shared__ R wv[kMaxDcD];
-  R* gsm;
-  int* gism;
-  smem_split<R>(smem_raw, g, true, a.smem_wm != 0, gsm, gism);
-  carve_zip<R>(g, p, zb, a.smem_wm ? gsm : nullptr, red, dred, wv, gsm, gism);
-  R* Hb = p; p += (size_t)(Lx + 1) * envT2;
-  R* Q[4];
-  for (int q = 0; q < 4; ++q) { Q[q] = p; p += envT2; }
-  R* t0 = p; p += tmp_elems(g);
-  R* t1 = p;
-  for (int i = threadIdx.x; i <= Lx; i += blockDim.x) ones[i] = 1;
-  __shared__ int eH[kMaxL + 1];   // H_c is stored scaled by 2^-eH[c]
-  const int nh = Ly * (Lx - 1);
-  for (int chain = blockIdx.x; chain < a.n; chain += gridDim.x) {
-    __syncthreads();
-    for (int i = threadIdx.x; i < g.nwords; i += blockDim.x) sp[i] = S[(size_t)chain * g.nwords + i];
-    __syncthreads();
-    long long acc = 0;
-    for (int k = 0; k < nsweeps; ++k) {
-      const uint64_t sweep = sweep0 + (uint64_t)k;
-      for (int pass = 0; pass < 2; ++pass) {
-        // lower environments L_r, r = Ly-1 .. 1, from the current S
-        const R* Min = a.triv_mps;
-        for (int j = 0; j + 1 < Ly; ++j) {
-          const int r = Ly - 1 - j;
-          const int* bdin = j == 0 ? ones : a.bd + ((size_t)1 * Ly + (j - 1)) * (Lx + 1);
-          R* Mout = envL + (size_t)r * Lx * envT;
-          absorb_row<R>(a, Min, Mout, r, 1, (j % 2) == 0, bdin, sp, zb, red);
-          Min = Mout;
-        }
-        const R* Mu = a.triv_mps;
-        int ub = 0;
-        const int rows = pass == 0 ? Ly : Ly - 1;
-        for (int r = 0; r < rows; ++r) {
-          const R* Md;
-          if (pass == 0) Md = r == Ly - 1 ? a.triv_mps : envL + (size_t)(r + 1) * Lx * envT;
-          else Md = r + 2 > Ly - 1 ? a.triv_mps : envL + (size_t)(r + 2) * Lx * envT;
-          const size_t tsz = pass == 0 ? envT : envT2;
-          const R* triv = pass == 0 ? a.triv_t1 : a.triv_t2;
-          for (size_t e = threadIdx.x; e < tsz; e += blockDim.x) Hb[(size_t)Lx * tsz + e] = triv[e];
-          if (threadIdx.x == 0) eH[Lx] = 0;
-          __syncthreads();
-          int eacc = 0;
-          for (int c = Lx - 1; c >= 0; --c) {
-            const int i1 = r * Lx + c;
-            if (pass == 0)
-              run_op<R>(OP_COL1_RIGHT, D, Dc, Hb + (size_t)(c + 1) * tsz, Mu + (size_t)c * envT,
-                        tptr(a, i1, spin_of(sp, i1)), Md + (size_t)c * envT, nullptr, Hb + (size_t)c * tsz, t0, t1, gsm, gism);
-            else
-              run_op<R>(OP_COL2_RIGHT, D, Dc, Hb + (size_t)(c + 1) * tsz, Mu + (size_t)c * envT,
-                        tptr(a, i1, spin_of(sp, i1)), tptr(a, i1 + Lx, spin_of(sp, i1 + Lx)),
-                        Md + (size_t)c * envT, Hb + (size_t)c * tsz, t0, t1, gsm, gism);
-            eacc += normalize_pow2(Hb + (size_t)c * tsz, (int)tsz, red);
-            if (threadIdx.x == 0) eH[c] = eacc;
-          }
-          const R* E = triv;
-          int e = 3;   // index in Q of the buffer E lives in (none yet)
-          const int ncol = pass == 0 ? Lx - 1 : Lx;
-          for (int c = 0; c < ncol; ++c) {
-            const int i1 = r * Lx + c;
-            const int i2 = pass == 0 ? i1 + 1 : i1 + Lx;
-            const int s1 = spin_of(sp, i1), s2 = spin_of(sp, i2);
-            R* X1 = Q[(e + 1) & 3];
-            R* Xf = Q[(e + 2) & 3];
-            R* X2 = Q[(e + 3) & 3];
-            const R* Muc = Mu + (size_t)c * envT;
-            const R* Mdc = Md + (size_t)c * envT;
-            int chosen;
-            if (s1 != s2) {
-              R w, wp;
-              if (pass == 0) {
-                run_op<R>(OP_COL1_LEFT, D, Dc, E, Muc, tptr(a, i1, s1), Mdc, nullptr, X1, t0, t1, gsm, gism);
-                run_op<R>(OP_COL1_LEFT, D, Dc, E, Muc, tptr(a, i1, s2), Mdc, nullptr, Xf, t0, t1, gsm, gism);
-                run_op<R>(OP_COL1_LEFT, D, Dc, Xf, Mu + (size_t)(c + 1) * envT, tptr(a, i2, s1),
-                          Md + (size_t)(c + 1) * envT, nullptr, X2, t0, t1, gsm, gism);
-                w = block_dot(X1, Hb + (size_t)(c + 1) * tsz, (int)tsz, red);
-                wp = block_dot(X2, Hb + (size_t)(c + 2) * tsz, (int)tsz, red);
-              } else {
-                run_op<R>(OP_COL2_LEFT, D, Dc, E, Muc, tptr(a, i1, s1), tptr(a, i2, s2), Mdc, X1, t0, t1, gsm, gism);
-                run_op<R>(OP_COL2_LEFT, D, Dc, E, Muc, tptr(a, i1, s2), tptr(a, i2, s1), Mdc, Xf, t0, t1, gsm, gism);
-                w = block_dot(X1, Hb + (size_t)(c + 1) * tsz, (int)tsz, red);
-                wp = block_dot(Xf, Hb + (size_t)(c + 1) * tsz, (int)tsz, red);
-              }
-              const uint64_t bond = pass == 0 ? (uint64_t)(r * (Lx - 1) + c) : (uint64_t)(nh + r * Lx + c);
-              const double u = sampler_uniform(seed, chain0 + (uint64_t)chain, sweep, bond);
-              bool take;
-              if (w == R(0)) {
-                take = true;
-              } else {
-                // the E scale is common to w and wp; the H scales differ by a column in a horizontal exchange
-                const double ratio =
-                    pass == 0 ? ldexp((double)wp / (double)w, eH[c + 2] - eH[c + 1]) : (double)wp / (double)w;
-                take = u < ratio * ratio;
-              }
-              if (take) {
-                if (threadIdx.x == 0) {
-                  sp[i1 >> 6] ^= 1ull << (i1 & 63);
-                  sp[i2 >> 6] ^= 1ull << (i2 & 63);
-                }
-                ++acc;
-                chosen = (e + 2) & 3;
-              } else {
-                chosen = (e + 1) & 3;
-              }
-              __syncthreads();
-            } else {
-              if (pass == 0)
-                run_op<R>(OP_COL1_LEFT, D, Dc, E, Muc, tptr(a, i1, s1), Mdc, nullptr, X1, t0, t1, gsm, gism);
-              else
-                run_op<R>(OP_COL2_LEFT, D, Dc, E, Muc, tptr(a, i1, s1), tptr(a, i2, s2), Mdc, X1, t0, t1, gsm, gism);
-              chosen = (e + 1) & 3;
-            }
-            e = chosen;
-            E = Q[e];
-            // E's own scale cancels in every ratio: renormalise without tracking
-            normalize_pow2(Q[e], (int)tsz, red);
-          }
-          if (pass == 0 ? (r < Ly - 1) : true) {
-            const int* bdin = r == 0 ? ones : a.bd + ((size_t)0 * Ly + (r - 1)) * (Lx + 1);
-            absorb_row<R>(a, Mu, Ubuf[ub], r, 0, (r % 2) == 0, bdin, sp, zb, red);
-            Mu = Ubuf[ub];
-            ub ^= 1;
-          }
-        }
-      }
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < g.nwords; i += blockDim.x) S[(size_t)chain * g.nwords + i] = sp[i];
-    if (threadIdx.x == 0 && accepted) accepted[chain] += acc;
-  }
 }
 
 // --------------------------------------------------------------- launchers
@@ -1151,195 +360,6 @@ cudaError_t launch_boundary(const KArgs<R>& a, int dirs, int grid, cudaStream_t 
   cudaError_t e = prefer_shared(k_boundary<R>, smem);
   if (e != cudaSuccess) return e;
   k_boundary<R><<<grid, kThreads, smem, st>>>(a, dirs);
-  return cudaGetLastError();
-}
-
-template <typename R>
-int max_blocks_mc(const Geometry& g) {
-  int dev = 0, nsm = 0, nb = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  const size_t smem = dyn_smem_bytes(g, sizeof(R), true, wm_fits_smem(g, sizeof(R)));
-  prefer_shared(k_mc<R>, smem);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_mc<R>, kThreads, smem);
-  if (nb < 1) nb = 1;
-  return nsm * nb;
-}
-
-template <typename R>
-cudaError_t launch_mc(const KArgs<R>& a, uint64_t* S, int nsweeps, uint64_t seed, uint64_t chain0, uint64_t sweep0,
-                      long long* accepted, int grid, cudaStream_t st) {
-  const size_t smem = dyn_smem_bytes(a.g, sizeof(R), true, a.smem_wm != 0);
-  cudaError_t e = prefer_shared(k_mc<R>, smem);
-  if (e != cudaSuccess) return e;
-  k_mc<R><<<grid, kThreads, smem, st>>>(a, S, nsweeps, seed, chain0, sweep0, accepted);
-  return cudaGetLastError();
-}
-
-// (D, Dc) pairs with a fused single-row step and site environment.
-template <typename R>
-static int row_fused_id(const Geometry& g) {
-  if (g.D == 2 && g.Dc == 4) return 1;
-  if (g.D == 4 && g.Dc == 8) return 2;
-  if (g.D == 6 && g.Dc == 12) return 3;
-  if (g.D == 8 && g.Dc == 16) return 4;
-  return 0;
-}
-
-template <typename R, int D, int Dc>
-static int row_fused_blocks() {
-  int dev = 0, nsm = 0, nb = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  const size_t smem = (size_t)RowSmem<D, Dc>::total * sizeof(R);
-  prefer_shared(k_row_fused<R, D, Dc>, smem);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_row_fused<R, D, Dc>, kThreads, smem);
-  return nsm * (nb < 1 ? 1 : nb);
-}
-
-template <typename R, int D, int Dc>
-static cudaError_t launch_row_fused(const KArgs<R>& a, int grid, cudaStream_t st) {
-  const size_t smem = (size_t)RowSmem<D, Dc>::total * sizeof(R);
-  cudaError_t e = prefer_shared(k_row_fused<R, D, Dc>, smem);
-  if (e != cudaSuccess) return e;
-  k_row_fused<R, D, Dc><<<grid, kThreads, smem, st>>>(a);
-  return cudaGetLastError();
-}
-
-template <typename R>
-int max_blocks_row(const Geometry& g) {
-  switch (row_fused_id<R>(g)) {
-    case 1: return row_fused_blocks<R, 2, 4>();
-    case 2: return row_fused_blocks<R, 4, 8>();
-    case 3: return row_fused_blocks<R, 6, 12>();
-    case 4: return row_fused_blocks<R, 8, 16>();
-  }
-  int dev = 0, nsm = 0, nb = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  const size_t smem = dyn_smem_bytes(g, sizeof(R), false, false);
-  prefer_shared(k_row<R>, smem);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_row<R>, kThreads, smem);
-  return nsm * (nb < 1 ? 1 : nb);
-}
-
-template <typename R>
-int max_blocks_pair(const Geometry& g) {
-  int dev = 0, nsm = 0, nb = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  const size_t smem = dyn_smem_bytes(g, sizeof(R), false, false);
-  prefer_shared(k_pair<R>, smem);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pair<R>, kThreads, smem);
-  return nsm * (nb < 1 ? 1 : nb);
-}
-
-template <typename R>
-cudaError_t launch_row(const KArgs<R>& a, int grid, cudaStream_t st) {
-  switch (row_fused_id<R>(a.g)) {
-    case 1: return launch_row_fused<R, 2, 4>(a, grid, st);
-    case 2: return launch_row_fused<R, 4, 8>(a, grid, st);
-    case 3: return launch_row_fused<R, 6, 12>(a, grid, st);
-    case 4: return launch_row_fused<R, 8, 16>(a, grid, st);
-  }
-  const size_t smem = dyn_smem_bytes(a.g, sizeof(R), false, false);
-  cudaError_t e = prefer_shared(k_row<R>, smem);
-  if (e != cudaSuccess) return e;
-  k_row<R><<<grid, kThreads, smem, st>>>(a);
-  return cudaGetLastError();
-}
-
-template <typename R, int D, int Dc>
-static cudaError_t launch_pair_fused(const KArgs<R>& a, int grid, cudaStream_t st) {
-  const size_t smem = (size_t)PairSmem<D, Dc>::total * sizeof(R);
-  cudaError_t e = prefer_shared(k_pair_fused<R, D, Dc>, smem);
-  if (e != cudaSuccess) return e;
-  k_pair_fused<R, D, Dc><<<grid, kThreads, smem, st>>>(a);
-  return cudaGetLastError();
-}
-
-template <typename R, int D, int Dc>
-static int fused_blocks() {
-  int dev = 0, nsm = 0, nb = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  const size_t smem = (size_t)PairSmem<D, Dc>::total * sizeof(R);
-  prefer_shared(k_pair_fused<R, D, Dc>, smem);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pair_fused<R, D, Dc>, kThreads, smem);
-  return nsm * (nb < 1 ? 1 : nb);
-}
-
-// (D, Dc) pairs with a fused two-row step; FP64 only where its shared memory fits.
-template <typename R>
-static int pair_fused_id(const Geometry& g) {
-  if (g.D == 2 && g.Dc == 4) return 1;
-  if (g.D == 4 && g.Dc == 8) return 2;
-  if (sizeof(R) == 4 && g.D == 6 && g.Dc == 12) return 3;
-  if (sizeof(R) == 4 && g.D == 8 && g.Dc == 16) return 4;
-  return 0;
-}
-
-template <typename R>
-int max_blocks_pair_fused(const Geometry& g) {
-  switch (pair_fused_id<R>(g)) {
-    case 1: return fused_blocks<R, 2, 4>();
-    case 2: return fused_blocks<R, 4, 8>();
-    case 3: return fused_blocks<R, sizeof(R) == 4 ? 6 : 2, sizeof(R) == 4 ? 12 : 4>();
-    case 4: return fused_blocks<R, sizeof(R) == 4 ? 8 : 2, sizeof(R) == 4 ? 16 : 4>();
-  }
-  return 0;
-}
-
-int max_blocks_pair_tc() {
-  int dev = 0, nsm = 0, nb = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  const size_t smem = (size_t)PairTcSmem::total * sizeof(float) + 1024;
-  prefer_shared(k_pair_tc, smem);
-  cudaFuncSetAttribute(k_pair_tc, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pair_tc, kThreads, smem);
-  // The occupancy query reports one resident CTA for this kernel, although
-  // its registers and shared memory fit two (as ncu's occupancy section also
-  // shows); take the residency from the kernel's own attributes as well.
-  cudaFuncAttributes fa{};
-  int smem_sm = 0, reserved = 0, regs_sm = 0;
-  if (cudaFuncGetAttributes(&fa, k_pair_tc) == cudaSuccess &&
-      cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) == cudaSuccess &&
-      cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) == cudaSuccess &&
-      cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev) == cudaSuccess &&
-      fa.numRegs > 0) {
-    const size_t per_block = fa.sharedSizeBytes + smem + (size_t)reserved;
-    const int by_smem = (int)((size_t)smem_sm / per_block);
-    const int by_regs = regs_sm / (fa.numRegs * kThreads);
-    nb = std::max(nb, std::min(by_smem, by_regs));
-  }
-  // each resident CTA holds kTmemCols of the SM's 512 TMEM columns
-  nb = std::min(nb, 512 / tc::kTmemCols);
-  return nsm * (nb < 1 ? 1 : nb);
-}
-
-cudaError_t launch_pair_tc(const KArgs<float>& a, int grid, cudaStream_t st) {
-  const size_t smem = (size_t)PairTcSmem::total * sizeof(float) + 1024;
-  cudaError_t e = prefer_shared(k_pair_tc, smem);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_pair_tc, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
-  if (e != cudaSuccess) return e;
-  k_pair_tc<<<grid, kThreads, smem, st>>>(a);
-  return cudaGetLastError();
-}
-
-template <typename R>
-cudaError_t launch_pair(const KArgs<R>& a, int grid, cudaStream_t st) {
-  switch (pair_fused_id<R>(a.g)) {
-    case 1: return launch_pair_fused<R, 2, 4>(a, grid, st);
-    case 2: return launch_pair_fused<R, 4, 8>(a, grid, st);
-    case 3: return launch_pair_fused<R, sizeof(R) == 4 ? 6 : 2, sizeof(R) == 4 ? 12 : 4>(a, grid, st);
-    case 4: return launch_pair_fused<R, sizeof(R) == 4 ? 8 : 2, sizeof(R) == 4 ? 16 : 4>(a, grid, st);
-  }
-  const size_t smem = dyn_smem_bytes(a.g, sizeof(R), false, false);
-  cudaError_t e = prefer_shared(k_pair<R>, smem);
-  if (e != cudaSuccess) return e;
-  k_pair<R><<<grid, kThreads, smem, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -1373,15 +393,7 @@ cudaError_t launch_grad_finalize(int total, int, const double* sums, const doubl
 
 #define PEPS_INST(R)                                                                                    \
   template int max_blocks_boundary<R>(const Geometry&);                                                 \
-  template int max_blocks_mc<R>(const Geometry&);                                                       \
-  template int max_blocks_row<R>(const Geometry&);                                                      \
-  template int max_blocks_pair<R>(const Geometry&);                                                     \
-  template int max_blocks_pair_fused<R>(const Geometry&);                                               \
-  template cudaError_t launch_mc<R>(const KArgs<R>&, uint64_t*, int, uint64_t, uint64_t, uint64_t,      \
-                                    long long*, int, cudaStream_t);                                      \
   template cudaError_t launch_boundary<R>(const KArgs<R>&, int, int, cudaStream_t);                     \
-  template cudaError_t launch_row<R>(const KArgs<R>&, int, cudaStream_t);                               \
-  template cudaError_t launch_pair<R>(const KArgs<R>&, int, cudaStream_t);                              \
   template cudaError_t launch_grad_accum<R>(const GradArgs&, const R*, cudaStream_t);
 PEPS_INST(double)
 PEPS_INST(float)
@@ -1426,10 +438,13 @@ __device__ void next_bonds(const int* bin, int* bout, int Lx, int D, int Dc, int
   }
 }
 
-__host__ __device__ inline size_t static_slot_elems(const Geometry& g, bool wm_in_smem) {
-  const size_t envT = (size_t)g.Dc * g.D * g.Dc, Dc = g.Dc, D = g.D, P = Dc * D;
-  const size_t zip = 2 * Dc * Dc * D + Dc * Dc * D * D + P * P + trunc_ws_elems((int)P, g.Dc, !wm_in_smem);
-  return (zip + 2 * (size_t)g.Lx * envT + 63) / 64 * 64;
+// A slot is what k_boundary's slot holds (the zip-up buffers carve_zip takes,
+// plus one boundary MPS) and one more boundary MPS: the sweep keeps the
+// current and the next MPS, where k_boundary writes the next one to the
+// environment array.
+static size_t static_slot_elems(const Geometry& g, bool wm_in_smem) {
+  const size_t envT = (size_t)g.Dc * g.D * g.Dc;
+  return (boundary_slot_elems(g, wm_in_smem) + (size_t)g.Lx * envT + 63) / 64 * 64;
 }
 
 template <typename R>
@@ -1509,24 +524,60 @@ __global__ void __launch_bounds__(kThreads) k_amplitudes_static(KArgs<R> a, R* s
   }
 }
 
-// Device address of the static scratch, looked up once per device with that
-// device current (the host-side symbol is only a stand-in, not an address).
-static void* g_static_ptr[256];
+// Device address of the static scratch.  In host code the array's name is a
+// stand-in, not a device address, so the address is looked up with
+// cudaGetSymbolAddress, with the device current, the first time a context
+// calls in.  The cache is keyed by the current CUDA context (not by the
+// device ordinal): after cudaDeviceReset, or under another context on the same
+// device, the module is loaded again at a new address, and the new context
+// misses the cache and looks the address up again.
+typedef int (*CtxGetCurrentFn)(void** ctx);
+
+static CtxGetCurrentFn ctx_get_current() {
+  static CtxGetCurrentFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (CtxGetCurrentFn)f;
+  }
+  return fn;
+}
+
+struct StaticPtr {
+  void* ctx;
+  void* ptr;
+};
+static StaticPtr g_static_ptr[64];
+static int g_static_n = 0;
 static std::mutex g_static_mu;
 
 static cudaError_t static_scratch_ptr(void** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= 256) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lock(g_static_mu);
-  if (!g_static_ptr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_static_scratch);
-    if (e != cudaSuccess) return e;
-    g_static_ptr[dev] = p;
+  CtxGetCurrentFn get = ctx_get_current();
+  void* ctx = nullptr;
+  if (get && get(&ctx) == 0 && ctx) {
+    for (int i = 0; i < g_static_n; ++i)
+      if (g_static_ptr[i].ctx == ctx) {
+        *out = g_static_ptr[i].ptr;
+        return cudaSuccess;
+      }
   }
-  *out = g_static_ptr[dev];
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);   // makes the device's context current if needed
+  if (e != cudaSuccess) return e;
+  ctx = nullptr;
+  if (get && get(&ctx) == 0 && ctx) {
+    int slot = -1;
+    for (int i = 0; i < g_static_n; ++i)
+      if (g_static_ptr[i].ctx == ctx) slot = i;
+    if (slot < 0) slot = g_static_n < 64 ? g_static_n++ : 0;
+    g_static_ptr[slot] = {ctx, p};
+  }
+  *out = p;
   return cudaSuccess;
 }
 

@@ -91,6 +91,12 @@ cudaError_t launch_grad_finalize(int total, int n_ok_dev_unused, const double* s
 // One gradient-optimisation update (Sec. III) of the FP64 tensors A [N][2][D^4] in place.
 cudaError_t launch_go_step(double* A, const double* grad, const Geometry& geo, double dt, uint64_t seed,
                            uint64_t step, int nsm, cudaStream_t st);
+// *bad |= 1 when a derivative of [N][2][D^4] is NaN or infinite.
+cudaError_t launch_go_check(const double* grad, const Geometry& geo, int* bad, int nsm, cudaStream_t st);
+// FP64 -> FP32 copy of n tensor entries.
+cudaError_t launch_to_f32(const double* a, float* b, size_t n, int nsm, cudaStream_t st);
+// Tensor-core B tiles (D = 8) of the FP64 site tensors [N][2][8^4].
+cudaError_t launch_tc_tiles(const double* A, float* tiles, int N, int nsm, cudaStream_t st);
 // Records the calling thread's error message (returned by peps_last_error).
 void set_last_error(const char* msg);
 

@@ -161,7 +161,7 @@ __device__ __forceinline__ void st4(float* p, float a, float b, float c, float d
 // as pair_step_fused, plus the pre-arranged B tiles of T1 (TA) and T2 (TB).
 // Returns <result, Hdot> when Hdot is given; otherwise writes the result
 // scaled by 2^-e to Eout and stores e in *e_out, as pair_step_fused.
-__device__ float pair_step_tc(PairTc& st, bool right, const float* Ein, float* __restrict__ Eout,
+static __device__ float pair_step_tc(PairTc& st, bool right, const float* Ein, float* __restrict__ Eout,
                               const float* __restrict__ Mu, const float* __restrict__ TA1,
                               const float* __restrict__ TB2, const float* __restrict__ Md,
                               const float* Hdot, float* sm, float* red, int* e_out = nullptr) {

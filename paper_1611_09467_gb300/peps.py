@@ -187,19 +187,26 @@ class PEPS:
 
     def set_tensors(self, A):
         A = _f64(A).copy()
-        assert A.shape == self.A.shape, A.shape
+        assert A.shape == (self.N, 2, self.D, self.D, self.D, self.D), A.shape
         check(lib().peps_set_tensors(self.h, _ptr(A)))
         self.A = A
 
-    def go_step(self, grad, dt, seed, step):
+    def go_step(self, grad, dt, seed, step, copy_back=True):
         """One gradient-optimisation update (Sec. III) with the derivative
-        ``grad`` (CUDA FP64 [N][2][D^4], e.g. ``gradient(S)["grad"]``); the
-        context then holds the new tensors.  Returns them (FP64, host)."""
+        ``grad`` (CUDA FP64 [N][2][D^4], e.g. ``gradient(S)["grad"]``), in
+        place on the device; the context then holds the new tensors.  With
+        ``copy_back`` they are also copied to the host and returned (FP64)."""
         torch = self.torch
         g = grad.to(device="cuda", dtype=torch.float64).contiguous()
-        assert g.numel() == self.A.size, g.shape
-        check(lib().peps_go_step(self.h, _ptr(g), float(dt), int(seed), int(step), _ptr(self.A)))
-        return self.A.copy()
+        shape = (self.N, 2, self.D, self.D, self.D, self.D)
+        assert g.numel() == int(np.prod(shape)), g.shape
+        out = np.empty(shape, dtype=np.float64) if copy_back else None
+        check(lib().peps_go_step(self.h, _ptr(g), float(dt), int(seed), int(step), _ptr(out)))
+        if copy_back:
+            self.A = out
+            return out.copy()
+        self.A = None          # the host copy is stale until the next copy_back
+        return None
 
     def evaluate(self, S, logabs=True, eloc=True, O=False):
         torch = self.torch

@@ -96,3 +96,15 @@ def test_exact_gradient_go_driver_descends():
     lines = [x.split() for x in r.stdout.splitlines() if x and not x.startswith("#")]
     e = [float(x[2]) for x in lines]
     assert len(e) == 3 and e[0] > e[1] > e[2] > -0.5
+
+
+def test_go_step_rejects_non_finite_derivatives():
+    """A NaN or infinite derivative has no sign to step against: the update
+    raises instead of moving (the GPU path refuses it with EINVAL)."""
+    A = inputs.make_tensors(3, 3, 2, seed=5)
+    g = np.ones((9, 2, 16))
+    for bad in (np.nan, np.inf, -np.inf):
+        gb = g.copy()
+        gb[4, 1, 3] = bad
+        with pytest.raises(ValueError):
+            O.go_step(A, gb, 0.004, 1, 0)
