@@ -27,6 +27,7 @@ Readings of what the paper leaves open (each in the design notes):
   shared site), first order.  With J2 != 0 the next-nearest gates follow:
   a diagonal pair (i, k) sharing neighbour j is done as SWAP(i, j), the gate
   on (j, k), SWAP(i, j), with a truncation after each two-site update.
+* Entries past an open edge are set back to zero after every update.
 * Gate: exp(-dtau J S_i.S_j) = e^{-dtau J/4} P_triplet + e^{3 dtau J/4} P_singlet
   (S.S is 1/4 on the triplet and -3/4 on the singlet).
 """
@@ -146,7 +147,11 @@ def bond_update(Gam, lam, i, j, G, Ly, Lx, D):
     for leg, b in bj.items():
         if leg != lj:
             Tj = _scale_leg(Tj, leg, _inv(lam[b]))
-    Gam[i], Gam[j] = Ti, Tj
+    # entries past an open edge stay zero (a rank-deficient split may leave
+    # rounding-sized values there)
+    from paper_1611_09467_gb300 import inputs
+    mask = inputs.edge_mask(Ly, Lx, D)
+    Gam[i], Gam[j] = Ti * mask[i], Tj * mask[j]
 
 
 def _inv(w):
