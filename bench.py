@@ -33,7 +33,6 @@ from paper_1611_09467_gb300 import inputs  # noqa: E402
 
 METRIC = "configs/s (psi+E_loc+dln psi) 16x16 D=8 Dc=16, mixed vs plain FP32; p99 ms"
 UNIT = "configs/s"
-FP32_SIMT_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per configuration
 # of the dominant kernel, from one ncu capture of 32 configurations of the
@@ -61,6 +60,12 @@ def parse():
                     help="serving benchmark: Poisson stream of requests over mixed lattices (continuous batching)")
     ap.add_argument("--serve-seconds", type=float, default=30.0)
     ap.add_argument("--lanes", type=int, default=4)
+    ap.add_argument("--autotune", action=argparse.BooleanOptionalAction, default=True,
+                    help="pick kernel variants and grids with peps_autotune on a probe batch first")
+    ap.add_argument("--graphs", action=argparse.BooleanOptionalAction, default=True,
+                    help="replay each step from a captured CUDA graph")
+    ap.add_argument("--workspace-gb", type=float, default=0.0,
+                    help="workspace budget (0: sized so one step's batch is one chunk, within half the free HBM)")
     return ap.parse_args()
 
 
@@ -164,10 +169,13 @@ def read_clocks(path, dev_index):
 def run_ours(args, rank, world, local_rank):
     import torch
     from paper_1611_09467_gb300 import build, flops
+    from paper_1611_09467_gb300.dist import distributed_gradient
     from paper_1611_09467_gb300.peps import PEPS
 
     build.build()
     torch.cuda.set_device(local_rank)
+    from paper_1611_09467_gb300.peps import measure_peaks
+    peaks = measure_peaks()
     w = inputs.WORKLOADS[args.workload]
     L, D, Dc, J2 = w["L"], w["D"], w["Dc"], w["J2"]
     n = args.n or w["n"]
@@ -175,12 +183,32 @@ def run_ours(args, rank, world, local_rank):
     # each rank draws its own configurations (weak scaling)
     spins = rank_configurations(args.workload, n, rank)
     S_host = torch.from_numpy(inputs.pack_spins(spins).view(np.int64)).pin_memory()
+    # the library's work goes to a stream of its own (graph capture needs one)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
     S = S_host.cuda()
-    p = PEPS(A, L, L, D, Dc, J1=1.0, J2=J2, prec=args.prec)
-    stream = torch.cuda.current_stream()
+    ws_gb = args.workspace_gb
+    if ws_gb <= 0:
+        # environments + Delta of the whole batch in one chunk where half the free HBM holds them
+        per_cfg = (2 * L * L * Dc * D * Dc + L * L * D ** 4) * (8 if args.prec == "fp64" else 4)
+        free = torch.cuda.mem_get_info()[0]
+        ws_gb = min(per_cfg * n * 1.02, 0.5 * free) / 1e9
+    p = PEPS(A, L, L, D, Dc, J1=1.0, J2=J2, prec=args.prec, workspace_gb=ws_gb)
+    tune_report = None
+    if args.autotune:
+        probe = S[: min(n, 608)].clone()
+        tune_report = p.autotune(probe)
+        del probe
+    if args.graphs and world == 1:
+        p.set_graphs(True)
+    outs = {}
 
     def step():
-        return p.gradient(S)
+        if world > 1:
+            # the one exchange of a multi-GPU gradient step: an allreduce of the sums
+            return distributed_gradient(p, S)
+        outs["g"] = p.gradient(S, out=outs.get("g"))
+        return outs["g"]
 
     for _ in range(args.warmup):
         step()
@@ -227,10 +255,12 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.synchronize()
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
+        Sd = torch.empty_like(S)
+        o = None
         t0.record(stream)
         for _ in range(args.steps):
-            Sd = S_host.to("cuda", non_blocking=True)
-            o = p.gradient(Sd, per_config=True)
+            Sd.copy_(S_host, non_blocking=True)
+            o = p.gradient(Sd, per_config=True, out=o)
             la_h.copy_(o["logabs"], non_blocking=True)
             el_h.copy_(o["eloc"], non_blocking=True)
         t1.record(stream)
@@ -241,31 +271,38 @@ def run_ours(args, rank, world, local_rank):
                "h2d_bytes_per_step": int(S_host.numel() * 8),
                "d2h_bytes_per_step": int(2 * n * 8 + 8)}
 
-    # roofline of the dominant kernel
+    # roofline of every kernel with a work model; the dominant one is the line's
     kern = {k: v for k, v in prof.items() if v[1] > 0}
     top = max(kern, key=lambda k: kern[k][0])
-    ms_top, launches_top = kern[top]
     sample = spins[: min(256, n)]
-    if top == "pair_sandwich":
-        f_cfg = flops.pair_flops_batch(L, L, D, Dc, sample, J2) / len(sample)
-    elif top == "row_sandwich":
-        f_cfg = flops.row_flops_batch(L, L, D, Dc, sample) / len(sample)
-    elif top == "boundary":
-        f_cfg = float(flops.boundary_flops(L, L, D, Dc))
-    else:
-        f_cfg = None
-    roofline = None
-    if f_cfg is not None:
-        flops_per_launch = f_cfg * n * args.steps / launches_top
-        achieved = flops_per_launch / (ms_top / launches_top / 1e3) / 1e12
-        cfg_per_launch = n * args.steps / launches_top
-        bpc = DRAM_BYTES_PER_CONFIG.get((args.workload, "float" if args.prec != "fp64" else "double", top))
-        roofline = {"bound": "alu", "kernel": top, "achieved": achieved, "peak": FP32_SIMT_TFLOPS,
-                    "unit": "TFLOP/s", "frac": achieved / FP32_SIMT_TFLOPS,
-                    "traffic": bpc * cfg_per_launch if bpc else None,
-                    "traffic_unit": "bytes per launch (DRAM read + write, ncu)",
-                    "peak_source": "FP32 SIMT: 152 SMs x 128 lanes x 2 flop x 2070 MHz (derived, nominal)",
-                    "flops_per_config": f_cfg}
+    tc = args.prec == "mixed_tf32" and (D, Dc) == (8, 16)
+    fp = "float" if args.prec != "fp64" else "double"
+
+    def roof(kname):
+        ms_k, launches_k = kern[kname]
+        if kname == "pair_sandwich":
+            f_cfg = flops.pair_flops_batch(L, L, D, Dc, sample, J2) / len(sample)
+        elif kname == "row_sandwich":
+            f_cfg = flops.row_flops_batch(L, L, D, Dc, sample) / len(sample)
+        elif kname == "boundary":
+            f_cfg = float(flops.boundary_flops(L, L, D, Dc))
+        else:
+            return None
+        achieved = f_cfg * n * args.steps / launches_k / (ms_k / launches_k / 1e3) / 1e12
+        if kname == "pair_sandwich" and tc:
+            peak, bound, src = peaks["tf32_tcgen05"], "tensor", "measured: dense TF32 tcgen05.mma (peps_measure_peaks)"
+        elif args.prec == "fp64":
+            peak, bound, src = peaks["fp64_simt"], "alu", "measured: FP64 FMA on the SIMT pipe (peps_measure_peaks)"
+        else:
+            peak, bound, src = peaks["fp32_simt"], "alu", "measured: FP32 FMA on the SIMT pipe (peps_measure_peaks)"
+        bpc = DRAM_BYTES_PER_CONFIG.get((args.workload, fp, kname))
+        return {"bound": bound, "kernel": kname, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": bpc * n * args.steps / launches_k if bpc else None,
+                "traffic_unit": "bytes per launch (DRAM read + write, ncu)", "peak_source": src,
+                "flops_per_config": f_cfg, "launches": launches_k}
+
+    roofline = roof(top)
+    other_roofs = {k: roof(k) for k in kern if k != top and roof(k) is not None}
     share = {k: round(v[0] / sum(x[0] for x in kern.values()), 4) for k, v in kern.items()}
     launches = sum(v[1] for v in kern.values())
     value = whole_job_rate(n, world, args.steps, total_ms)
@@ -281,16 +318,22 @@ def run_ours(args, rank, world, local_rank):
                                                     "FP32 SIMT (the tcgen05 two-row step covers D=8, Dc=16)"}[args.prec],
                    "sampling": "uniform random Sz=0 configurations",
                    "l2": "working set per step (environments, Delta) is tens of GB, far above L2",
-                   "parallelism": f"dp{world} (independent configurations)"},
+                   "parallelism": f"dp{world} (independent configurations"
+                                  + ("; one allreduce of the gradient sums per step)" if world > 1 else ")")},
         "whole_step_ms": {"median": statistics.median(per_step), "max": max(per_step),
                           "what": "device time of whole timed steps (one batch each), not request latencies; "
                                   "request latency p50/p99 is the --serve line's"},
         "kernel_share": share, "gpu_launches": launches, "roofline": roofline, "clocks": clocks, "e2e": e2e,
-        "energy_per_site": out["energy_per_site"],
+        "energy_per_site": out["energy_per_site"], "roofline_other_kernels": other_roofs,
+        "peaks_measured_tflops": peaks,
     }
+    res["config"]["tiles"] = p.tuned_config()
+    res["config"]["graphs"] = bool(args.graphs and world == 1)
+    if tune_report:
+        res["config"]["autotune"] = tune_report
     if args.compare_fp32 and args.prec != "fp32":
         p.close()
-        q = PEPS(A, L, L, D, Dc, J1=1.0, J2=J2, prec="fp32")
+        q = PEPS(A, L, L, D, Dc, J1=1.0, J2=J2, prec="fp32", workspace_gb=ws_gb)
         q.gradient(S)
         torch.cuda.synchronize()
         c0 = torch.cuda.Event(enable_timing=True)
@@ -337,34 +380,42 @@ def run_serving(args):
 
     # per-model latency alone on one lane (also creates the workers), then the
     # sustained capacity: a closed-loop burst of 4 requests per lane, timed
+    def finish(server, done):
+        # drop the finished requests' outputs (Delta of a large request is GBs)
+        for rid, _ in done:
+            server.outputs.pop(rid, None)
+        return [x for _, x in done]
+
     probe_ms = []
     for k in range(len(models)):
         _, S = make_request(k, 10_000 + k)
-        srv.submit(models[k], S)
+        srv.submit(models[k], S, O=True)
         done = srv.drain()
         probe_ms.append(done[0][1])
+        finish(srv, done)
     burst = [make_request(int(rng.integers(len(models))), 15_000 + i) for i in range(4 * args.lanes)]
     torch.cuda.synchronize()
     tb = time.perf_counter()
     for k, S in burst:
-        srv.submit(models[k], S)
-    srv.drain()
+        srv.submit(models[k], S, O=True)
+    finish(srv, srv.drain())
     capacity = len(burst) / (time.perf_counter() - tb)                 # requests/s, all lanes busy
-    rate = 0.7 * capacity
+    rate = 0.8 * capacity
     arrivals = poisson_arrivals(rate, args.serve_seconds, inputs.SEED_BASE + 5)
     reqs = [make_request(int(rng.integers(len(models))), 20_000 + i) for i in range(len(arrivals))]
     torch.cuda.synchronize()
     srv2 = Server(nlanes=args.lanes, hbm_budget_gb=budget)
+    srv2.set_packing(512, 4)
     clk_serve = os.path.join(tempfile.gettempdir(), "peps_bench_clocks_serve.csv")
     sampler, fh = start_clock_sampler(clk_serve)
     t0 = time.perf_counter()
     lat = []
     for (k, S), ta in zip(reqs, arrivals):
         while time.perf_counter() - t0 < ta:
-            lat += [x for _, x in srv2.poll(wait=False)]
+            lat += finish(srv2, srv2.poll(wait=False))
             time.sleep(0.0005)
-        srv2.submit(models[k], S)
-    lat += [x for _, x in srv2.drain()]
+        srv2.submit(models[k], S, O=True)
+    lat += finish(srv2, srv2.drain())
     wall = time.perf_counter() - t0
     if sampler:
         sampler.terminate()
@@ -373,13 +424,15 @@ def run_serving(args):
     st = srv2.stats()
     total = sum(int(S.shape[0]) for _, S in reqs)
     res = {
-        "metric": "serving: aggregate configs/s (psi+E_loc) and request latency p50/p99 ms, mixed lattices",
+        "metric": "serving: aggregate configs/s (psi+E_loc+dln psi) and request latency p50/p99 ms, mixed lattices",
         "value": total / wall, "unit": "configs/s", "n_gpus": 1, "higher_is_better": True,
         "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
         "requests": len(reqs), "configs": total, "wall_s": wall, "data": "synthetic",
         "config": {"mix": [dict(L=L, D=D, Dc=Dc, J2=J2, prec=pr) for (L, D, Dc, J2, pr) in SERVE_MIX],
-                   "configs_per_request": "uniform 256..1024", "arrivals": f"Poisson, {rate:.2f}/s "
-                   f"(70% of the closed-loop capacity {capacity:.2f}/s)", "lanes": args.lanes, "hbm_budget_gb": budget,
+                   "configs_per_request": "uniform 256..1024", "outputs": "ln|psi|, sign, E_loc, Delta",
+                   "arrivals": f"Poisson, {rate:.2f}/s (80% of the closed-loop capacity {capacity:.2f}/s)",
+                   "packing": "requests of <= 512 configurations, up to 4 models per launch",
+                   "lanes": args.lanes, "hbm_budget_gb": budget,
                    "duration_s": args.serve_seconds},
         "server": st, "probe_ms_per_model": probe_ms,
         "clocks": read_clocks(clk_serve, 0),

@@ -139,6 +139,28 @@ peps_status peps_gradient(peps_ctx* ctx, const uint64_t* S_dev, int n, double* e
                           double* cov_dev, double* logabs_dev, int8_t* sign_dev, double* eloc_dev,
                           int32_t* status_dev, int* n_used_host);
 
+/* The sums behind peps_gradient's estimates, for reductions across batches
+ * or ranks: the estimator of Sec. II is built from sums over configurations,
+ * so the sums of disjoint batches add (one allreduce across GPUs) before
+ * peps_gradient_finalize forms the means.  sums_dev is a device array of
+ * peps_gradient_sums_len(ctx) = 4 + 2 N 2 D^4 doubles:
+ *   [0] sum of E(S), [1] number of configurations used, [2] sum of E(S)^2,
+ *   [3] zero, then sum of Delta [N][2][D^4] (zero in the block a
+ *   configuration's spin does not select), then sum of E(S) Delta [N][2][D^4],
+ * over the configurations with status 0.  accumulate = 0 overwrites the
+ * sums, 1 adds to them.  Per-configuration outputs as in peps_gradient. */
+peps_status peps_gradient_sums(peps_ctx* ctx, const uint64_t* S_dev, int n, double* sums_dev, int accumulate,
+                               double* logabs_dev, int8_t* sign_dev, double* eloc_dev, int32_t* status_dev);
+size_t peps_gradient_sums_len(const peps_ctx* ctx);
+
+/* Energy and gradient from sums laid out as above (e.g. after adding the
+ * sums of every rank): energy per site <E>/N, the sample variance of E/N
+ * (var(E)/N^2, NaN below two configurations), grad_dev = 2(<Delta E> -
+ * <Delta><E>), cov_dev = grad/2 (Sec. II).  Every output may be NULL.
+ * Synchronises the context's stream. */
+peps_status peps_gradient_finalize(peps_ctx* ctx, const double* sums_dev, double* energy_per_site_host,
+                                   double* energy_var_host, double* grad_dev, double* cov_dev, int* n_used_host);
+
 /* nsweeps Metropolis sweeps per configuration (chain), in place on S_dev.
  * A sweep visits the nearest-neighbour bonds in the order: horizontal
  * row-major, then vertical row-major; an antiparallel pair is exchanged with
@@ -150,6 +172,104 @@ peps_status peps_gradient(peps_ctx* ctx, const uint64_t* S_dev, int n, double* e
  * by the number of accepted exchanges. */
 peps_status peps_mc_sweep(peps_ctx* ctx, uint64_t* S_dev, int n, int nsweeps, uint64_t seed, uint64_t chain0,
                           uint64_t sweep0, int64_t* accepted_dev);
+
+/* Sampled spin-spin correlations and the staggered magnetisation (Sec. IV).
+ * For configurations drawn with weight W^2 the local value of S_i.S_j
+ * (i != j) is S^z_i S^z_j + [s_i != s_j] W(S^ij) / (2 W(S)), S^ij with s_i and
+ * s_j exchanged; the paper's M^2 is (1/n^2) sum_{p,q} eps_p eps_q <S_p.S_q>
+ * over n central sites, eps = (-1)^(row + col) (k = (pi, pi)).  Reading of
+ * the ratio for a pair i < j in rows r_i <= r_j: the configuration's upper
+ * environment U_{r_i - 1} absorbs row r_i with s_i flipped and the rows
+ * below it (zip-up truncation to Dc, Fig. 1d); in row r_j it meets the row
+ * with s_j flipped and the lower environment L_{r_j + 1} in a single-row
+ * sandwich, divided by the configuration's own single-row sandwich of row
+ * r_j, with the difference of the per-row norms the two sweeps divided out.
+ * Exact when nothing is truncated.  Cost per configuration: one partial
+ * boundary sweep per central site.
+ *   sites_host [nc]: distinct central sites (host); m2_dev [n] (optional):
+ *   the local M^2 of each configuration (NaN where status != 0);
+ *   corr_dev [nc][nc] (optional): the sums over the configurations with
+ *   status 0 of the local S_p.S_q (3/4 on the diagonal; divide by their
+ *   number for the estimates); status_dev [n] (optional) as peps_evaluate. */
+peps_status peps_correlations(peps_ctx* ctx, const uint64_t* S_dev, int n, const int* sites_host, int nc,
+                              double* m2_dev, double* corr_dev, int32_t* status_dev);
+
+/* Environment cache.  With on != 0 a context keeps, next to the boundary
+ * environments in its workspace, a copy of the configurations they belong
+ * to.  A later peps_evaluate, peps_gradient or peps_correlations call whose
+ * batch fits in one chunk compares each configuration with the cached one on
+ * the device, and where the bits are unchanged (same slot, same tensors,
+ * same workspace) skips that configuration's boundary sweeps, keeping its
+ * ln|psi|, sign and environments; a changed configuration (a new request, a
+ * Metropolis move) is swept again.  So amplitudes, then E_loc, then Delta of
+ * one batch sweep the boundary once, and so does an evaluation after a
+ * Metropolis sweep for the chains that did not move.  Results are
+ * bit-identical to calls without the cache.  The cache is reset by
+ * peps_set_tensors, peps_go_step, a batch larger than one chunk, or a packed
+ * launch that used the context. */
+peps_status peps_set_env_cache(peps_ctx* ctx, int on);
+
+/* ---- batching: graphs, tuning, packed launches ----
+ * CUDA-graph replay.  With on != 0, peps_evaluate and peps_gradient capture
+ * the device work of a call (every chunk's kernel launches, memsets and
+ * copies, and the read-back of the energy into page-locked memory) into a
+ * CUDA graph on the first call with a given signature (S_dev, n and the
+ * output pointers), instantiate it, and replay it on later calls with the
+ * same signature: the launch sequence is issued once per call instead of
+ * kernel by kernel.  Up to 16 signatures are kept; all are dropped when the
+ * context's workspace buffers move (a larger batch) and when graphs are
+ * turned off.  Results are bit-identical to calls without graphs.  Needs a
+ * context created on a non-default stream (PEPS_EINVAL otherwise).  While
+ * capturing, per-kernel profiling events are not recorded. */
+peps_status peps_set_graphs(peps_ctx* ctx, int on);
+/* stats[3]: graphs cached, captures and replays since the context was created. */
+peps_status peps_graph_stats(peps_ctx* ctx, long long* stats);
+
+/* Autotuner.  Times full gradient passes (one untimed, one timed, CUDA
+ * events on the context's stream) over the probe batch S_dev [n] for each
+ * candidate, one setting after another, and keeps the fastest:
+ *   - the two-row kernel: tensor cores (PEPS_MIXED_TF32, D = 8, Dc = 16),
+ *     the fused shared-memory kernel (where one exists for (D, Dc)), or the
+ *     generic one;
+ *   - the single-row kernel: fused (where one exists) or generic;
+ *   - the persistent grid of the boundary sweeps: the resident CTA count or
+ *     half of it;
+ *   - the workspace budget (configurations per chunk): the current one, x2,
+ *     x4 (within 60% of device memory), tried only when the probe batch
+ *     spans more than one chunk.
+ * The variants compute the same quantities; FP32 results may differ in the
+ * last bits between variants.  The choice is kept in the context and in a
+ * process-wide table: contexts created later for the same (Lx, Ly, D, Dc,
+ * precision, SM count) start with it.  report (optional, report_len bytes)
+ * receives every trial's time and the choice.  Synchronises the stream. */
+peps_status peps_autotune(peps_ctx* ctx, const uint64_t* S_dev, int n, char* report, size_t report_len);
+
+/* The context's kernel settings: vals[0] two-row kernel (0 tensor cores,
+ * 1 fused, 2 generic), vals[1] single-row kernel (0 fused, 1 generic),
+ * vals[2] boundary-sweep CTAs, vals[3] configurations per chunk of the last
+ * call; *workspace_gb the workspace budget. */
+peps_status peps_tuned_config(peps_ctx* ctx, int* vals /* [4] */, double* workspace_gb);
+
+/* Packed launches.  A packer evaluates requests of several models (contexts
+ * of different lattices, D and Dc, all PEPS_FP64 or all of the FP32 family)
+ * with the boundary sweeps of all requests in ONE persistent kernel launch:
+ * work items are (request, configuration, sweep direction) numbered request
+ * after request, each CTA finds its request by the item's index and lays its
+ * scratch slot and shared memory out for that model.  The sandwich and
+ * finalisation steps then run per request.  Everything runs on the packer's
+ * stream (cudaStream_t, NULL = legacy default) using each context's
+ * workspace, so the contexts must have no work in flight on their own
+ * streams.  Per request i: S[i] [n[i]][ceil(N_i/64)], outputs as in
+ * peps_evaluate (each array of pointers, or any of its entries, may be
+ * NULL); a request must fit in one chunk of its context's workspace
+ * (PEPS_EINVAL otherwise) and a context may appear once per call.  Results
+ * are bit-identical to peps_evaluate on each context alone. */
+typedef struct peps_packer peps_packer;
+peps_status peps_packer_create(void* cuda_stream, peps_packer** out);
+peps_status peps_packer_destroy(peps_packer* packer);
+peps_status peps_packer_evaluate(peps_packer* packer, int nreq, peps_ctx* const* ctxs, const uint64_t* const* S_dev,
+                                 const int* n, double* const* logabs_dev, int8_t* const* sign_dev,
+                                 double* const* eloc_dev, void* const* O_dev, int32_t* const* status_dev);
 
 /* Per-kernel timing of this context's launches: when enabled, CUDA events
  * are recorded on the context's stream around every kernel the library
@@ -186,6 +306,39 @@ peps_status peps_profile_read(peps_ctx* ctx, double* ms /* [8] */, long long* la
 peps_status peps_amplitudes_static(const peps_params* params, const void* A_dev, const uint64_t* S_dev, int n,
                                    double* logabs_dev, int8_t* sign_dev, int32_t* status_dev, void* cuda_stream);
 
+/* ---- simple-update initialiser (Sec. III, computational details) ----
+ * Imaginary-time evolution exp(-dtau H) of the J1-J2 Heisenberg model by
+ * first-order Trotter steps of two-site gates, each applied with the simple
+ * update: the weights of the bonds around the pair are absorbed, a QR of each
+ * site tensor isolates the bond (O(D^5)), the gate acts on the reduced
+ * tensors, an SVD cuts the bond back to D and its D largest singular values
+ * (normalised to unit 2-norm) become the bond's new weight.  A step applies
+ * the horizontal bonds at even then odd columns, the vertical bonds at even
+ * then odd rows, and with J2 != 0 each next-nearest pair (i, k) as
+ * SWAP(i, j), gate(j, k), SWAP(i, j) through their shared neighbour j.  Each
+ * group of bonds without a shared site is one launch, one CTA per bond, in
+ * FP64.  The paper runs dtau = 0.01 until the relative change of the tensors
+ * falls below 1e-6, then dtau = 0.001.
+ *   State, caller-owned device arrays (FP64):
+ *     Gam_dev [N][2][D^4]: Gamma_i[s][l][r][u][d], padded like A, zero past open edges;
+ *     lam_dev [nbonds][D]: bond weights, bonds numbered horizontal (row-major)
+ *                          then vertical (row-major), nbonds = Ly(Lx-1) + (Ly-1)Lx.
+ *   peps_su_create: params' Lx, Ly, D, J1, J2 (Dc, prec unused); the handle owns
+ *     the bond tables and per-CTA scratch (4 D^3 2D doubles per bond of a group).
+ *   peps_su_evolve: nsteps Trotter steps with time step dtau (>= 0), in place;
+ *     change_host (optional) receives max|A' - A| / max|A| over the last step,
+ *     A the PEPS of peps_su_to_peps (synchronises the stream when given).
+ *   peps_su_to_peps: A_dev [N][2][D^4] = Gamma_i times sqrt(lam) on each of its
+ *     bonds, scaled to unit Frobenius norm per site (the tensors of Eq. 1 that
+ *     peps_create takes).
+ * Work is enqueued on the handle's stream; errors: PEPS_EINVAL (arguments),
+ * PEPS_ENOMEM / PEPS_ECUDA. */
+typedef struct peps_su peps_su;
+peps_status peps_su_create(const peps_params* params, void* cuda_stream, peps_su** out);
+peps_status peps_su_destroy(peps_su* su);
+peps_status peps_su_evolve(peps_su* su, double* Gam_dev, double* lam_dev, double dtau, int nsteps, double* change_host);
+peps_status peps_su_to_peps(peps_su* su, const double* Gam_dev, const double* lam_dev, double* A_dev);
+
 /* ---- serving: continuous batching of evaluation requests ----
  * A server owns `nlanes` lanes (CUDA streams).  Each request asks for the
  * outputs of peps_evaluate for n configurations of one model (a context
@@ -205,6 +358,24 @@ peps_status peps_server_destroy(peps_server* server);
 peps_status peps_server_submit(peps_server* server, peps_ctx* model, const uint64_t* S_dev, int n,
                                double* logabs_dev, int8_t* sign_dev, double* eloc_dev, void* O_dev,
                                int32_t* status_dev, long long* id_out);
+/* A chain request: the Markov chains' configurations S_dev (device, owned
+ * by the caller, kept there between requests) first take nsweeps Metropolis
+ * sweeps in place (peps_mc_sweep's keyed draws: seed, chain0, sweep0), then
+ * are evaluated as by peps_server_submit.  Lane workers keep their boundary
+ * environments (peps_set_env_cache) and a chain's request prefers the lane
+ * that served the same S_dev last, so chains that did not move are not swept
+ * again. */
+peps_status peps_server_submit_chain(peps_server* server, peps_ctx* model, uint64_t* S_dev, int n, int nsweeps,
+                                     uint64_t seed, uint64_t chain0, uint64_t sweep0, double* logabs_dev,
+                                     int8_t* sign_dev, double* eloc_dev, void* O_dev, int32_t* status_dev,
+                                     long long* id_out);
+/* Packing: a free lane that admits a request of at most max_configs
+ * configurations also takes up to max_requests - 1 further queued ones of
+ * other models (same precision class, each within max_configs, all within
+ * the HBM budget) and runs them as one packed launch (peps_packer_evaluate):
+ * their boundary sweeps share one kernel.  max_configs = 0 (the default)
+ * turns packing off.  Results equal the requests run alone. */
+peps_status peps_server_set_packing(peps_server* server, int max_configs, int max_requests);
 /* Retires finished requests and admits queued ones.  wait != 0 blocks until
  * at least one request finishes (or nothing is left).  Up to max finished ids
  * and their latencies (ms, submission to completion) are written; *ndone is
@@ -215,6 +386,14 @@ peps_status peps_server_poll(peps_server* server, int wait, long long* ids, doub
 /* stats[8]: submitted, completed, queued, running, p50 and p99 latency (ms),
  * HBM in use and peak HBM (GB) of the lanes' workspaces. */
 peps_status peps_server_stats(peps_server* server, double* stats);
+
+/* Measured throughput of the pipes the kernels run on, for roofline
+ * denominators: out[0] FP32 fused multiply-add on the SIMT pipe, out[1] FP64
+ * likewise, out[2] dense TF32 tcgen05.mma (FP32 accumulation), in TFLOP/s.
+ * Long independent chains on every SM, timed with CUDA events; synchronises
+ * the device.  PEPS_ETIMEOUT if the tensor-core probe's bounded wait gave up.
+ * The paper has no counterpart. */
+peps_status peps_measure_peaks(double* out /* [3] */);
 
 /* Waits for the context's stream. */
 peps_status peps_synchronize(peps_ctx* ctx);

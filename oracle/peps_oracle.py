@@ -494,7 +494,7 @@ def sampler_uniform(seed: int, chain: int, sweep: int, bond: int) -> float:
     return (h >> 11) * 2.0 ** -53
 
 
-def mc_sweep(A, spins, Ly, Lx, Dc, seed, chain, sweep):
+def mc_sweep(A, spins, Ly, Lx, Dc, seed, chain, sweep, decisions=None):
     """One Metropolis sweep over the nearest-neighbour bonds; returns (spins, accepted).
 
     The move exchanges the two spins of an antiparallel NN pair (this keeps
@@ -506,6 +506,10 @@ def mc_sweep(A, spins, Ly, Lx, Dc, seed, chain, sweep):
     pass; the upper environment grows row by row from the updated rows.
     Vertical pass: the same, recomputed at its start, with the two-row
     sandwich <U_{r-1}| rows r, r+1 |L_{r+2}>.
+
+    ``decisions`` (diagnostic, default None): a list that receives
+    (bond index, (W(S')/W(S))^2, u) for every decision taken, so that a test
+    can tell which decisions sat close to their threshold.
     """
     spins = np.array(spins, dtype=np.int64)
     h_bonds, v_bonds = nn_bonds(Ly, Lx)
@@ -539,6 +543,8 @@ def mc_sweep(A, spins, Ly, Lx, Dc, seed, chain, sweep):
             w, wp = float(Fw.reshape(-1)[0]), float(Fp.reshape(-1)[0])
             ratio2 = (wp / w) ** 2 if w != 0.0 else math.inf
             u = sampler_uniform(seed, chain, sweep, b)
+            if decisions is not None:
+                decisions.append((b, ratio2, u))
             if u < ratio2:
                 spins[i], spins[j] = spins[j], spins[i]
                 accepted += 1
@@ -572,6 +578,8 @@ def mc_sweep(A, spins, Ly, Lx, Dc, seed, chain, sweep):
             w, wp = float(Ew.reshape(-1)[0]), float(Ep.reshape(-1)[0])
             ratio2 = (wp / w) ** 2 if w != 0.0 else math.inf
             u = sampler_uniform(seed, chain, sweep, b)
+            if decisions is not None:
+                decisions.append((b, ratio2, u))
             if u < ratio2:
                 spins[i], spins[j] = spins[j], spins[i]
                 accepted += 1

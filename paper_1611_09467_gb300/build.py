@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT, "libpeps.so")
-SOURCES = ["kernels.cu", "row.cu", "pair.cu", "mc.cu", "api.cu", "serve.cu"]
+SOURCES = ["kernels.cu", "row.cu", "pair.cu", "mc.cu", "corr.cu", "su.cu", "peaks.cu", "api.cu", "serve.cu"]
 INCLUDE = os.path.join(ROOT, "include")
 
 

@@ -1,8 +1,10 @@
 // C ABI of libpeps.so: context, workspace, batching into chunks, launches.
 #include <algorithm>
+#include <functional>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -114,6 +116,31 @@ struct peps_ctx {
   int chunk = 0;  // configurations per pass
   int res_boundary = 0, res_row = 0, res_pair = 0, res_mc = 0;  // resident CTAs per kernel
   bool pair_tc = false;  // two-row step on the tensor cores (PEPS_MIXED_TF32, D = 8, Dc = 16)
+  // kernel variants (peps_autotune): row_generic 1 takes the generic single-row
+  // kernel; pair_mode 0 the default two-row kernel (tensor cores where
+  // pair_tc, else fused where one exists), 1 the fused SIMT kernel, 2 the generic one
+  int row_generic = 0, pair_mode = 0;
+  int boundary_ctas = 0;   // 0: the boundary kernel's resident CTA count, else this many (peps_autotune)
+  DevBuf corr_sites, corr_x, corr_scratch;   // correlation functions (peps_correlations)
+  // environment cache (peps_set_env_cache): the bits of the configurations
+  // whose boundary sweeps are in env, and per configuration which sweeps are
+  bool env_cache = false, cache_dirty = true;
+  DevBuf Scache, cbits;
+  unsigned long long tensor_gen = 0, env_gen = 0, cache_key = ~0ull;
+  // CUDA-graph replay (peps_set_graphs): one instantiated graph per call signature
+  bool graphs = false, capturing = false;
+  struct GraphEntry {
+    int op;
+    const void* S;
+    int n;
+    const void* out[6];
+    unsigned long long gen;
+    cudaGraphExec_t exec;
+  };
+  std::vector<GraphEntry> gcache;
+  unsigned long long ws_gen = 0;   // bumped whenever a workspace buffer moves
+  long long graph_captures = 0, graph_replays = 0;
+  double* pinned = nullptr;        // 4 doubles of page-locked host memory for graph read-backs
   // profiling: event pairs per kernel id
   bool prof = false;
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev;
@@ -129,14 +156,14 @@ struct Prof {
   cudaEvent_t a = nullptr, b = nullptr;
   Prof(peps_ctx* c_, int id_) : c(c_), id(id_) {
     c->launches[id] += 1;
-    if (c->prof) {
+    if (c->prof && !c->capturing) {
       cudaEventCreate(&a);
       cudaEventCreate(&b);
       cudaEventRecord(a, c->stream);
     }
   }
   ~Prof() {
-    if (c->prof) {
+    if (c->prof && !c->capturing) {
       cudaEventRecord(b, c->stream);
       c->ev.push_back({id, {a, b}});
     }
@@ -153,6 +180,7 @@ double* master_tensors(peps_ctx* c) { return c->elem == 8 ? (double*)c->A.p : (d
 // The working copies derived on the device from the FP64 master: the FP32
 // tensors and, on the tensor-core path, the pre-arranged TF32 B tiles.
 peps_status refresh_working_copies(peps_ctx* c) {
+  ++c->tensor_gen;   // cached environments belong to the old tensors
   const size_t D4 = (size_t)c->g.D * c->g.D * c->g.D * c->g.D;
   const size_t nel = (size_t)c->g.N * 2 * D4;
   if (c->elem == 4) {
@@ -206,11 +234,12 @@ struct Small {
   double* eloc_h;
   double* eloc_v;
   double* w_row;
+  double* lnU;
   int* flags;
   int* status;
   int8_t* sign;
   static size_t bytes(int chunk, int Ly) {
-    return (size_t)chunk * (2 + 3 * (size_t)Ly) * 8 + (size_t)chunk * 2 * 4 + (size_t)chunk + 256;
+    return (size_t)chunk * (2 + 4 * (size_t)Ly) * 8 + (size_t)chunk * 2 * 4 + (size_t)chunk + 256;
   }
   void carve(void* base, int chunk, int Ly) {
     char* p = (char*)base;
@@ -219,6 +248,7 @@ struct Small {
     eloc_h = (double*)p; p += (size_t)chunk * Ly * 8;
     eloc_v = (double*)p; p += (size_t)chunk * Ly * 8;
     w_row = (double*)p; p += (size_t)chunk * Ly * 8;
+    lnU = (double*)p; p += (size_t)chunk * Ly * 8;
     flags = (int*)p; p += (size_t)chunk * 4;
     status = (int*)p; p += (size_t)chunk * 4;
     sign = (int8_t*)p;
@@ -247,10 +277,15 @@ peps_status ensure_workspace(peps_ctx* c, int n, bool want_O) {
   int chunk = (int)std::max<double>(1.0, std::floor(budget / (double)per_cfg));
   chunk = std::min(chunk, std::max(n, 1));
   c->chunk = chunk;
+  const void* before[4] = {c->env.p, c->small.p, c->O.p, c->scratch.p};
   PEPS_CUDA(c->env.ensure(env_bytes_per_cfg(c) * chunk));
   PEPS_CUDA(c->small.ensure(Small::bytes(chunk, g.Ly)));
   if (want_O) PEPS_CUDA(c->O.ensure((size_t)chunk * g.N * D4 * c->elem));
   PEPS_CUDA(c->scratch.ensure(slot_elems(c) * c->elem * c->nslots));
+  const void* after[4] = {c->env.p, c->small.p, c->O.p, c->scratch.p};
+  for (int i = 0; i < 4; ++i)
+    if (before[i] != after[i]) ++c->ws_gen;   // captured graphs that read the old buffers are stale
+  if (before[0] != after[0] || before[1] != after[1]) ++c->env_gen;   // cached environments are gone
   return PEPS_OK;
 }
 
@@ -259,6 +294,7 @@ KArgs<R> make_args(peps_ctx* c, const uint64_t* S, int n, const Small& sm) {
   KArgs<R> a;
   const Geometry& g = c->g;
   a.g = g;
+  a.cache = nullptr;
   a.A = (const R*)c->A.p;
   a.triv_mps = (const R*)c->triv_mps.p;
   a.triv_t1 = (const R*)c->triv_t1.p;
@@ -275,6 +311,7 @@ KArgs<R> make_args(peps_ctx* c, const uint64_t* S, int n, const Small& sm) {
   a.eloc_h = sm.eloc_h;
   a.eloc_v = sm.eloc_v;
   a.w_row = sm.w_row;
+  a.lnU = sm.lnU;
   a.O = nullptr;
   a.scratch = (R*)c->scratch.p;
   a.slot_elems = slot_elems(c);
@@ -283,46 +320,84 @@ KArgs<R> make_args(peps_ctx* c, const uint64_t* S, int n, const Small& sm) {
   return a;
 }
 
+// Single-row and two-row sandwich steps and the E(S)/status finalisation of
+// one chunk whose environments are in place, on stream st.
 template <typename R>
-peps_status evaluate_chunk(peps_ctx* c, const uint64_t* S, int n, bool need_env_l, bool need_pairs, R* O,
-                           Small& sm) {
-  KArgs<R> a = make_args<R>(c, S, n, sm);
-  a.O = O;
-  PEPS_CUDA(cudaMemsetAsync(sm.flags, 0, (size_t)n * sizeof(int), c->stream));
-  const int dirs = need_env_l ? 2 : 1;
-  // persistent kernels: never more CTAs than can be resident at once
-  int grid = std::min(n * dirs, std::min(c->nslots, c->res_boundary));
-  {
-    Prof pf(c, 0);
-    PEPS_CUDA(launch_boundary<R>(a, dirs, std::max(grid, 1), c->stream));
-  }
+peps_status sandwich_chunk(peps_ctx* c, const KArgs<R>& a, const uint64_t* S, int n, bool need_env_l,
+                           bool need_pairs, Small& sm, cudaStream_t st) {
+  int grid;
   if (need_env_l) {
     grid = std::min(n * c->g.Ly, std::min(c->nslots, c->res_row));
     Prof pf(c, 1);
-    PEPS_CUDA(launch_row<R>(a, std::max(grid, 1), c->stream));
+    PEPS_CUDA(launch_row<R>(a, std::max(grid, 1), st, c->row_generic));
   }
   if (need_pairs && c->g.Ly > 1) {
     grid = std::min(n * (c->g.Ly - 1), std::min(c->nslots, c->res_pair));
     Prof pf(c, 2);
     if constexpr (sizeof(R) == 4) {
-      if (c->pair_tc) {
-        PEPS_CUDA(launch_pair_tc(a, std::max(grid, 1), c->stream));
+      if (c->pair_tc && c->pair_mode == 0) {
+        PEPS_CUDA(launch_pair_tc(a, std::max(grid, 1), st));
       } else {
-        PEPS_CUDA(launch_pair<R>(a, std::max(grid, 1), c->stream));
+        PEPS_CUDA(launch_pair<R>(a, std::max(grid, 1), st, c->pair_mode == 2));
       }
     } else {
-      PEPS_CUDA(launch_pair<R>(a, std::max(grid, 1), c->stream));
+      PEPS_CUDA(launch_pair<R>(a, std::max(grid, 1), st, c->pair_mode == 2));
     }
   } else {
-    PEPS_CUDA(cudaMemsetAsync(sm.eloc_v, 0, (size_t)n * c->g.Ly * sizeof(double), c->stream));
+    PEPS_CUDA(cudaMemsetAsync(sm.eloc_v, 0, (size_t)n * c->g.Ly * sizeof(double), st));
   }
-  if (!need_env_l) PEPS_CUDA(cudaMemsetAsync(sm.eloc_h, 0, (size_t)n * c->g.Ly * sizeof(double), c->stream));
+  if (!need_env_l) PEPS_CUDA(cudaMemsetAsync(sm.eloc_h, 0, (size_t)n * c->g.Ly * sizeof(double), st));
   {
     Prof pf(c, 3);
     PEPS_CUDA(launch_finalize(c->g, S, n, sm.eloc_h, sm.eloc_v, sm.flags, sm.eloc, sm.status, need_env_l ? 1 : 0,
-                              c->stream));
+                              st));
   }
   return PEPS_OK;
+}
+
+// Environment cache for a call whose batch is one chunk: configurations whose
+// bits equal the cached copy keep their boundary sweeps (k_cache_check clears
+// the bits of the others).  The cache is reset when the tensors, the
+// workspace or the chunk size changed, or after a call that wrote the
+// environments without it.
+template <typename R>
+peps_status prepare_cache(peps_ctx* c, const uint64_t* S, int n, bool whole_batch, KArgs<R>& a) {
+  if (!c->env_cache || !whole_batch) {
+    c->cache_dirty = true;
+    return PEPS_OK;
+  }
+  const Geometry& g = c->g;
+  const void* p0[2] = {c->Scache.p, c->cbits.p};
+  PEPS_CUDA(c->Scache.ensure((size_t)c->chunk * g.nwords * sizeof(uint64_t)));
+  PEPS_CUDA(c->cbits.ensure((size_t)c->chunk * sizeof(unsigned)));
+  const unsigned long long key = (c->tensor_gen * 1000003ull + c->env_gen) * 1000003ull + (unsigned long long)c->chunk;
+  if (c->cache_dirty || key != c->cache_key || p0[0] != c->Scache.p || p0[1] != c->cbits.p) {
+    PEPS_CUDA(cudaMemsetAsync(c->cbits.p, 0, (size_t)c->chunk * sizeof(unsigned), c->stream));
+    c->cache_dirty = false;
+    c->cache_key = key;
+  }
+  PEPS_CUDA(launch_cache_check(S, (uint64_t*)c->Scache.p, (unsigned*)c->cbits.p, n, g.nwords, c->stream));
+  a.cache = (unsigned*)c->cbits.p;
+  return PEPS_OK;
+}
+
+template <typename R>
+peps_status evaluate_chunk(peps_ctx* c, const uint64_t* S, int n, bool need_env_l, bool need_pairs, R* O,
+                           Small& sm, bool whole_batch = false) {
+  KArgs<R> a = make_args<R>(c, S, n, sm);
+  a.O = O;
+  peps_status cst = prepare_cache<R>(c, S, n, whole_batch, a);
+  if (cst != PEPS_OK) return cst;
+  PEPS_CUDA(cudaMemsetAsync(sm.flags, 0, (size_t)n * sizeof(int), c->stream));
+  const int dirs = need_env_l ? 2 : 1;
+  // persistent kernels: never more CTAs than can be resident at once
+  const int res = c->boundary_ctas > 0 ? std::min(c->boundary_ctas, c->res_boundary) : c->res_boundary;
+  int grid = std::min(n * dirs, std::min(c->nslots, res));
+  {
+    Prof pf(c, 0);
+    PEPS_CUDA(launch_boundary<R>(a, dirs, std::max(grid, 1), c->stream));
+  }
+  return sandwich_chunk<R>(c, a, S, n, need_env_l, need_pairs, sm, c->stream);
 }
 
 peps_status check_ctx(peps_ctx* c, const void* S, int n) {
@@ -347,7 +422,7 @@ peps_status evaluate_impl(peps_ctx* c, const uint64_t* S, int n, double* logabs,
   for (int c0 = 0; c0 < n; c0 += c->chunk) {
     const int m = std::min(c->chunk, n - c0);
     const uint64_t* Sc = S + (size_t)c0 * g.nwords;
-    st = evaluate_chunk<R>(c, Sc, m, need_l, want_e, want_O ? O + (size_t)c0 * g.N * D4 : nullptr, sm);
+    st = evaluate_chunk<R>(c, Sc, m, need_l, want_e, want_O ? O + (size_t)c0 * g.N * D4 : nullptr, sm, m == n);
     if (st != PEPS_OK) return st;
     if (logabs) PEPS_CUDA(cudaMemcpyAsync(logabs + c0, sm.logabs, m * 8, cudaMemcpyDeviceToDevice, c->stream));
     if (sign) PEPS_CUDA(cudaMemcpyAsync(sign + c0, sm.sign, m, cudaMemcpyDeviceToDevice, c->stream));
@@ -357,25 +432,33 @@ peps_status evaluate_impl(peps_ctx* c, const uint64_t* S, int n, double* logabs,
   return PEPS_OK;
 }
 
+// Layout of the gradient sums (doubles), also the public layout of
+// peps_gradient_sums: [0] sum E, [1] count, [2] sum E^2, [3] zero, then
+// sum O [N][2][D^4], then sum E*O [N][2][D^4].
+constexpr size_t kSumsHead = 4;
+
+size_t grad_total(const peps_ctx* c) {
+  const Geometry& g = c->g;
+  return (size_t)g.N * 2 * g.D * g.D * g.D * g.D;
+}
+
 template <typename R>
-peps_status gradient_impl(peps_ctx* c, const uint64_t* S, int n, double* e_site, double* grad, double* cov,
-                          double* logabs, int8_t* sign, double* eloc, int32_t* status, int* n_used) {
+peps_status gradient_sums_impl(peps_ctx* c, const uint64_t* S, int n, double* sums, bool accumulate,
+                               double* logabs, int8_t* sign, double* eloc, int32_t* status) {
   const Geometry& g = c->g;
   const size_t D4 = (size_t)g.D * g.D * g.D * g.D;
-  const size_t total = (size_t)g.N * 2 * D4;
+  const size_t total = grad_total(c);
   peps_status st = ensure_workspace(c, n, true);
   if (st != PEPS_OK) return st;
-  PEPS_CUDA(c->gsum.ensure((2 * total + 2) * sizeof(double)));
-  double* sumO = (double*)c->gsum.p;
+  double* sumO = sums + kSumsHead;
   double* sumEO = sumO + total;
-  double* sums = sumEO + total;
-  PEPS_CUDA(cudaMemsetAsync(c->gsum.p, 0, (2 * total + 2) * sizeof(double), c->stream));
+  if (!accumulate) PEPS_CUDA(cudaMemsetAsync(sums, 0, (kSumsHead + 2 * total) * sizeof(double), c->stream));
   Small sm;
   sm.carve(c->small.p, c->chunk, g.Ly);
   for (int c0 = 0; c0 < n; c0 += c->chunk) {
     const int m = std::min(c->chunk, n - c0);
     const uint64_t* Sc = S + (size_t)c0 * g.nwords;
-    st = evaluate_chunk<R>(c, Sc, m, true, true, (R*)c->O.p, sm);
+    st = evaluate_chunk<R>(c, Sc, m, true, true, (R*)c->O.p, sm, m == n);
     if (st != PEPS_OK) return st;
     GradArgs ga;
     ga.N = g.N;
@@ -400,16 +483,35 @@ peps_status gradient_impl(peps_ctx* c, const uint64_t* S, int n, double* e_site,
     if (eloc) PEPS_CUDA(cudaMemcpyAsync(eloc + c0, sm.eloc, m * 8, cudaMemcpyDeviceToDevice, c->stream));
     if (status) PEPS_CUDA(cudaMemcpyAsync(status + c0, sm.status, m * 4, cudaMemcpyDeviceToDevice, c->stream));
   }
-  {
+  return PEPS_OK;
+}
+
+peps_status gradient_finalize_impl(peps_ctx* c, const double* sums, double* e_site, double* e_var, double* grad,
+                                   double* cov, int* n_used) {
+  const size_t total = grad_total(c);
+  if (grad || cov) {
     Prof pf(c, 6);
-    PEPS_CUDA(launch_grad_finalize((int)total, 0, sums, sumO, sumEO, grad, cov, c->stream));
+    PEPS_CUDA(launch_grad_finalize((int)total, 0, sums, sums + kSumsHead, sums + kSumsHead + total, grad, cov,
+                                   c->stream));
   }
-  double h[2] = {0, 0};
+  double h[3] = {0, 0, 0};
   PEPS_CUDA(cudaMemcpyAsync(h, sums, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
   PEPS_CUDA(cudaStreamSynchronize(c->stream));
-  if (e_site) *e_site = h[1] > 0 ? h[0] / h[1] / g.N : NAN;
+  const double N = c->g.N;
+  if (e_site) *e_site = h[1] > 0 ? h[0] / h[1] / N : NAN;
+  if (e_var) *e_var = h[1] > 1 ? (h[2] - h[0] * h[0] / h[1]) / (h[1] - 1) / (N * N) : NAN;
   if (n_used) *n_used = (int)h[1];
   return PEPS_OK;
+}
+
+template <typename R>
+peps_status gradient_impl(peps_ctx* c, const uint64_t* S, int n, double* e_site, double* grad, double* cov,
+                          double* logabs, int8_t* sign, double* eloc, int32_t* status, int* n_used) {
+  const size_t total = grad_total(c);
+  PEPS_CUDA(c->gsum.ensure((kSumsHead + 2 * total) * sizeof(double)));
+  peps_status st = gradient_sums_impl<R>(c, S, n, (double*)c->gsum.p, false, logabs, sign, eloc, status);
+  if (st != PEPS_OK) return st;
+  return gradient_finalize_impl(c, (const double*)c->gsum.p, e_site, nullptr, grad, cov, n_used);
 }
 
 template <typename R>
@@ -424,6 +526,242 @@ peps_status mc_impl(peps_ctx* c, uint64_t* S, int n, int nsweeps, uint64_t seed,
   const int grid = std::min(n, std::min(c->nslots, c->res_mc));
   Prof pf(c, 7);
   PEPS_CUDA(launch_mc<R>(a, S, nsweeps, seed, chain0, sweep0, (long long*)accepted, std::max(grid, 1), c->stream));
+  return PEPS_OK;
+}
+
+// ------------------------------------------------------------ CUDA graphs
+void drop_graphs(peps_ctx* c) {
+  for (auto& e : c->gcache) cudaGraphExecDestroy(e.exec);
+  c->gcache.clear();
+}
+
+// Runs `enqueue` (work enqueued on the context's stream only, no host
+// synchronisation) through an instantiated CUDA graph: the first call with a
+// signature (op, S, n, outputs) and the current workspace captures and
+// instantiates it, later calls replay it.  Graphs are dropped when the
+// workspace buffers move (ws_gen).
+template <typename F>
+peps_status run_graphed(peps_ctx* c, int op, const void* S, int n, const void* const out[6], F enqueue) {
+  for (auto& e : c->gcache) {
+    bool same = e.op == op && e.S == S && e.n == n && e.gen == c->ws_gen;
+    for (int i = 0; same && i < 6; ++i) same = e.out[i] == out[i];
+    if (same) {
+      PEPS_CUDA(cudaGraphLaunch(e.exec, c->stream));
+      ++c->graph_replays;
+      return PEPS_OK;
+    }
+  }
+  cudaGraph_t graph = nullptr;
+  PEPS_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+  c->capturing = true;
+  peps_status st = enqueue();
+  c->capturing = false;
+  cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
+  if (st != PEPS_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return st;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+  cudaGraphExec_t exec = nullptr;
+  e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+  if (c->gcache.size() >= 16) {
+    cudaGraphExecDestroy(c->gcache.front().exec);
+    c->gcache.erase(c->gcache.begin());
+  }
+  peps_ctx::GraphEntry ge;
+  ge.op = op;
+  ge.S = S;
+  ge.n = n;
+  for (int i = 0; i < 6; ++i) ge.out[i] = out[i];
+  ge.gen = c->ws_gen;
+  ge.exec = exec;
+  c->gcache.push_back(ge);
+  ++c->graph_captures;
+  PEPS_CUDA(cudaGraphLaunch(exec, c->stream));
+  return PEPS_OK;
+}
+
+peps_status ensure_pinned(peps_ctx* c) {
+  if (!c->pinned) PEPS_CUDA(cudaMallocHost((void**)&c->pinned, 4 * sizeof(double)));
+  return PEPS_OK;
+}
+
+template <typename R>
+peps_status gradient_graphed(peps_ctx* c, const uint64_t* S, int n, double* e_site, double* grad, double* cov,
+                             double* logabs, int8_t* sign, double* eloc, int32_t* status, int* n_used) {
+  const size_t total = grad_total(c);
+  const void* g0 = c->gsum.p;
+  PEPS_CUDA(c->gsum.ensure((kSumsHead + 2 * total) * sizeof(double)));
+  if (c->gsum.p != g0) ++c->ws_gen;
+  peps_status st = ensure_workspace(c, n, true);
+  if (st == PEPS_OK) st = ensure_pinned(c);
+  if (st != PEPS_OK) return st;
+  const void* out[6] = {grad, cov, logabs, sign, eloc, status};
+  double* sums = (double*)c->gsum.p;
+  st = run_graphed(c, 1, S, n, out, [&]() -> peps_status {
+    peps_status s2 = gradient_sums_impl<R>(c, S, n, sums, false, logabs, sign, eloc, status);
+    if (s2 != PEPS_OK) return s2;
+    if (grad || cov) {
+      Prof pf(c, 6);
+      PEPS_CUDA(launch_grad_finalize((int)total, 0, sums, sums + kSumsHead, sums + kSumsHead + total, grad, cov,
+                                     c->stream));
+    }
+    PEPS_CUDA(cudaMemcpyAsync(c->pinned, sums, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    return PEPS_OK;
+  });
+  if (st != PEPS_OK) return st;
+  PEPS_CUDA(cudaStreamSynchronize(c->stream));
+  const double* h = c->pinned;
+  if (e_site) *e_site = h[1] > 0 ? h[0] / h[1] / c->g.N : NAN;
+  if (n_used) *n_used = (int)h[1];
+  return PEPS_OK;
+}
+
+// ------------------------------------------------------------ kernel variants
+// Resident CTA counts for the chosen single- and two-row kernels.
+void apply_variants(peps_ctx* c) {
+  const Geometry& g = c->g;
+  if (c->elem == 8) {
+    c->res_row = max_blocks_row<double>(g, c->row_generic);
+    const int fused = max_blocks_pair_fused<double>(g);
+    c->res_pair = (c->pair_mode == 2 || !fused) ? max_blocks_pair<double>(g) : fused;
+  } else {
+    c->res_row = max_blocks_row<float>(g, c->row_generic);
+    const int fused = max_blocks_pair_fused<float>(g);
+    if (c->pair_tc && c->pair_mode == 0) c->res_pair = max_blocks_pair_tc();
+    else c->res_pair = (c->pair_mode == 2 || !fused) ? max_blocks_pair<float>(g) : fused;
+  }
+  c->nslots = std::max(std::max(c->res_boundary, c->res_row), std::max(c->res_pair, c->res_mc));
+}
+
+struct TuneKey {
+  int Lx, Ly, D, Dc, prec, nsm;
+  bool operator==(const TuneKey& o) const {
+    return Lx == o.Lx && Ly == o.Ly && D == o.D && Dc == o.Dc && prec == o.prec && nsm == o.nsm;
+  }
+};
+struct TuneVal {
+  int row_generic, pair_mode, boundary_ctas;
+  double workspace_gb;
+};
+std::vector<std::pair<TuneKey, TuneVal>> g_tuned;   // choices of peps_autotune in this process
+std::mutex g_tune_mu;
+
+TuneKey tune_key(const peps_ctx* c) { return {c->g.Lx, c->g.Ly, c->g.D, c->g.Dc, c->p.prec, c->nsm}; }
+
+// ------------------------------------------------------------ packed launches
+template <typename R>
+peps_status packed_impl(peps_packer* pk, int nreq, peps_ctx* const* ctxs, const uint64_t* const* S, const int* n,
+                        double* const* logabs, int8_t* const* sign, double* const* eloc, void* const* O,
+                        int32_t* const* status);
+
+}  // namespace
+
+struct peps_packer {
+  cudaStream_t stream = nullptr;
+  DevBuf scratch, models, start;
+  int nsm = 0;
+};
+
+namespace {
+
+template <typename R>
+peps_status packed_impl(peps_packer* pk, int nreq, peps_ctx* const* ctxs, const uint64_t* const* S, const int* n,
+                        double* const* logabs, int8_t* const* sign, double* const* eloc, void* const* O,
+                        int32_t* const* status) {
+  bool any_env = false;
+  for (int i = 0; i < nreq; ++i) any_env = any_env || (eloc && eloc[i]) || (O && O[i]);
+  const int dirs = any_env ? 2 : 1;
+  std::vector<KArgs<R>> args(nreq);
+  std::vector<Small> sms(nreq);
+  std::vector<int> start(nreq + 1, 0);
+  size_t slot = 0, smem = 0;
+  for (int i = 0; i < nreq; ++i) {
+    peps_ctx* c = ctxs[i];
+    peps_status st = ensure_workspace(c, n[i], false);
+    if (st != PEPS_OK) return st;
+    if (n[i] > c->chunk)
+      return fail(PEPS_EINVAL, "a packed request must fit in one chunk of its context's workspace");
+    sms[i].carve(c->small.p, c->chunk, c->g.Ly);
+    args[i] = make_args<R>(c, S[i], n[i], sms[i]);
+    c->cache_dirty = true;   // the packed launch writes this context's environments without the cache
+    args[i].O = (O && O[i]) ? (R*)O[i] : nullptr;
+    PEPS_CUDA(cudaMemsetAsync(sms[i].flags, 0, (size_t)n[i] * sizeof(int), pk->stream));
+    start[i + 1] = start[i] + n[i] * dirs;
+    slot = std::max(slot, boundary_slot_elems(c->g, c->wm_smem));
+    smem = std::max(smem, dyn_smem_bytes(c->g, sizeof(R), true, c->wm_smem));
+  }
+  slot = (slot + 31) / 32 * 32;
+  const int total = start[nreq];
+  const int grid = std::max(1, std::min(total, max_blocks_boundary_packed<R>(smem)));
+  PEPS_CUDA(pk->scratch.ensure(slot * sizeof(R) * grid));
+  PEPS_CUDA(pk->models.ensure(sizeof(KArgs<R>) * nreq));
+  PEPS_CUDA(pk->start.ensure(sizeof(int) * (nreq + 1)));
+  // pageable sources: the copies have taken the data when the calls return
+  PEPS_CUDA(cudaMemcpyAsync(pk->models.p, args.data(), sizeof(KArgs<R>) * nreq, cudaMemcpyHostToDevice, pk->stream));
+  PEPS_CUDA(cudaMemcpyAsync(pk->start.p, start.data(), sizeof(int) * (nreq + 1), cudaMemcpyHostToDevice, pk->stream));
+  PEPS_CUDA(launch_boundary_packed<R>((const KArgs<R>*)pk->models.p, (const int*)pk->start.p, nreq, dirs,
+                                      (R*)pk->scratch.p, slot, smem, grid, pk->stream));
+  for (int i = 0; i < nreq; ++i) {
+    peps_ctx* c = ctxs[i];
+    const bool want_e = eloc && eloc[i], want_O = O && O[i];
+    peps_status st = sandwich_chunk<R>(c, args[i], S[i], n[i], want_e || want_O, want_e, sms[i], pk->stream);
+    if (st != PEPS_OK) return st;
+    const int m = n[i];
+    if (logabs && logabs[i])
+      PEPS_CUDA(cudaMemcpyAsync(logabs[i], sms[i].logabs, m * 8, cudaMemcpyDeviceToDevice, pk->stream));
+    if (sign && sign[i]) PEPS_CUDA(cudaMemcpyAsync(sign[i], sms[i].sign, m, cudaMemcpyDeviceToDevice, pk->stream));
+    if (want_e) PEPS_CUDA(cudaMemcpyAsync(eloc[i], sms[i].eloc, m * 8, cudaMemcpyDeviceToDevice, pk->stream));
+    if (status && status[i])
+      PEPS_CUDA(cudaMemcpyAsync(status[i], sms[i].status, m * 4, cudaMemcpyDeviceToDevice, pk->stream));
+  }
+  return PEPS_OK;
+}
+
+// ------------------------------------------------------------ correlations
+template <typename R>
+peps_status correlations_impl(peps_ctx* c, const uint64_t* S, int n, const int* sites, int nc, double* m2,
+                              double* corr, int32_t* status) {
+  const Geometry& g = c->g;
+  peps_status st = ensure_workspace(c, n, false);
+  if (st != PEPS_OK) return st;
+  std::vector<int> tab((size_t)nc + g.N, -1);
+  for (int p = 0; p < nc; ++p) {
+    tab[p] = sites[p];
+    tab[(size_t)nc + sites[p]] = p;
+  }
+  PEPS_CUDA(c->corr_sites.ensure(tab.size() * sizeof(int)));
+  PEPS_CUDA(cudaMemcpyAsync(c->corr_sites.p, tab.data(), tab.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+  PEPS_CUDA(c->corr_x.ensure((size_t)c->chunk * sizeof(double)));
+  const int res = max_blocks_corr<R>(g);
+  const size_t slot = (corr_slot_elems(g, c->wm_smem) + 31) / 32 * 32;
+  PEPS_CUDA(c->corr_scratch.ensure(slot * c->elem * res));
+  if (corr) PEPS_CUDA(cudaMemsetAsync(corr, 0, (size_t)nc * nc * sizeof(double), c->stream));
+  CorrArgs ca;
+  ca.sites = (const int*)c->corr_sites.p;
+  ca.pos = (const int*)c->corr_sites.p + nc;
+  ca.nc = nc;
+  ca.xsum = (double*)c->corr_x.p;
+  ca.corr = corr;
+  ca.slot_elems = slot;
+  Small sm;
+  sm.carve(c->small.p, c->chunk, g.Ly);
+  for (int c0 = 0; c0 < n; c0 += c->chunk) {
+    const int m = std::min(c->chunk, n - c0);
+    const uint64_t* Sc = S + (size_t)c0 * g.nwords;
+    st = evaluate_chunk<R>(c, Sc, m, true, false, nullptr, sm, m == n);
+    if (st != PEPS_OK) return st;
+    KArgs<R> a = make_args<R>(c, Sc, m, sm);
+    a.scratch = (R*)c->corr_scratch.p;
+    ca.status = sm.status;
+    PEPS_CUDA(cudaMemsetAsync(ca.xsum, 0, (size_t)m * sizeof(double), c->stream));
+    const int grid = std::max(1, std::min(m * nc, res));
+    PEPS_CUDA(launch_corr<R>(a, ca, grid, c->stream));
+    PEPS_CUDA(launch_corr_finalize(g, ca, Sc, m, sm.status, m2 ? m2 + c0 : nullptr, c->stream));
+    if (status) PEPS_CUDA(cudaMemcpyAsync(status + c0, sm.status, m * 4, cudaMemcpyDeviceToDevice, c->stream));
+  }
   return PEPS_OK;
 }
 
@@ -482,6 +820,8 @@ size_t ctx_workspace_bytes(peps_ctx* c) {
 }
 
 cudaStream_t ctx_stream(peps_ctx* c) { return c->stream; }
+
+bool ctx_is_fp64(const peps_ctx* c) { return c->elem == 8; }
 
 }  // namespace peps
 
@@ -562,6 +902,18 @@ peps_status peps_create(const peps_params* p, const double* A_host, void* stream
     c->res_mc = max_blocks_mc<float>(c->g);
   }
   c->nslots = std::max(std::max(c->res_boundary, c->res_row), std::max(c->res_pair, c->res_mc));
+  {
+    // a choice peps_autotune made in this process for the same model shape
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    for (auto& kv : g_tuned)
+      if (kv.first == tune_key(c)) {
+        c->row_generic = kv.second.row_generic;
+        c->pair_mode = kv.second.pair_mode;
+        c->boundary_ctas = kv.second.boundary_ctas;
+        if (c->p.workspace_gb <= 0) c->p.workspace_gb = kv.second.workspace_gb;
+        apply_variants(c);
+      }
+  }
   peps_status st = upload_tensors(c, A_host);
   if (st == PEPS_OK) st = c->elem == 8 ? setup_trivial<double>(c) : setup_trivial<float>(c);
   if (st != PEPS_OK) {
@@ -580,7 +932,10 @@ peps_status peps_destroy(peps_ctx* c) {
     cudaEventDestroy(e.second.first);
     cudaEventDestroy(e.second.second);
   }
-  DevBuf* work[] = {&c->env, &c->small, &c->O, &c->scratch, &c->gsum, &c->go};
+  drop_graphs(c);
+  if (c->pinned) cudaFreeHost(c->pinned);
+  DevBuf* work[] = {&c->env, &c->small, &c->O, &c->scratch, &c->gsum, &c->go, &c->corr_sites, &c->corr_x,
+                    &c->corr_scratch, &c->Scache, &c->cbits};
   for (DevBuf* b : work) b->release();
   if (!c->parent) {
     DevBuf* model[] = {&c->tcB, &c->A, &c->A64, &c->triv_mps, &c->triv_t1, &c->triv_t2, &c->bd};
@@ -624,6 +979,16 @@ peps_status peps_evaluate(peps_ctx* c, const uint64_t* S, int n, double* logabs,
   peps_status st = check_ctx(c, S, n);
   if (st != PEPS_OK) return st;
   g_err.clear();
+  if (c->graphs && n > 0) {
+    peps_status st0 = ensure_workspace(c, n, false);
+    if (st0 != PEPS_OK) return st0;
+    const void* out[6] = {logabs, sign, eloc, O, status, nullptr};
+    if (c->elem == 8)
+      return run_graphed(c, 0, S, n, out,
+                         [&]() { return evaluate_impl<double>(c, S, n, logabs, sign, eloc, (double*)O, status); });
+    return run_graphed(c, 0, S, n, out,
+                       [&]() { return evaluate_impl<float>(c, S, n, logabs, sign, eloc, (float*)O, status); });
+  }
   if (c->elem == 8) return evaluate_impl<double>(c, S, n, logabs, sign, eloc, (double*)O, status);
   return evaluate_impl<float>(c, S, n, logabs, sign, eloc, (float*)O, status);
 }
@@ -649,9 +1014,37 @@ peps_status peps_gradient(peps_ctx* c, const uint64_t* S, int n, double* e_site,
   if (st != PEPS_OK) return st;
   if (n == 0) return fail(PEPS_EINVAL, "empty batch");
   g_err.clear();
+  if (c->graphs) {
+    if (c->elem == 8) return gradient_graphed<double>(c, S, n, e_site, grad, cov, logabs, sign, eloc, status, n_used);
+    return gradient_graphed<float>(c, S, n, e_site, grad, cov, logabs, sign, eloc, status, n_used);
+  }
   if (c->elem == 8) return gradient_impl<double>(c, S, n, e_site, grad, cov, logabs, sign, eloc, status, n_used);
   return gradient_impl<float>(c, S, n, e_site, grad, cov, logabs, sign, eloc, status, n_used);
 }
+
+peps_status peps_gradient_sums(peps_ctx* c, const uint64_t* S, int n, double* sums, int accumulate, double* logabs,
+                               int8_t* sign, double* eloc, int32_t* status) {
+  peps_status st = check_ctx(c, S, n);
+  if (st != PEPS_OK) return st;
+  if (!sums) return fail(PEPS_EINVAL, "null sums");
+  g_err.clear();
+  if (n == 0) {
+    if (!accumulate)
+      PEPS_CUDA(cudaMemsetAsync(sums, 0, (kSumsHead + 2 * grad_total(c)) * sizeof(double), c->stream));
+    return PEPS_OK;
+  }
+  if (c->elem == 8) return gradient_sums_impl<double>(c, S, n, sums, accumulate != 0, logabs, sign, eloc, status);
+  return gradient_sums_impl<float>(c, S, n, sums, accumulate != 0, logabs, sign, eloc, status);
+}
+
+peps_status peps_gradient_finalize(peps_ctx* c, const double* sums, double* e_site, double* e_var, double* grad,
+                                   double* cov, int* n_used) {
+  if (!c || !sums) return fail(PEPS_EINVAL, "null argument");
+  g_err.clear();
+  return gradient_finalize_impl(c, sums, e_site, e_var, grad, cov, n_used);
+}
+
+size_t peps_gradient_sums_len(const peps_ctx* c) { return c ? kSumsHead + 2 * grad_total(c) : 0; }
 
 peps_status peps_mc_sweep(peps_ctx* c, uint64_t* S, int n, int nsweeps, uint64_t seed, uint64_t chain0,
                           uint64_t sweep0, int64_t* accepted) {
@@ -661,6 +1054,216 @@ peps_status peps_mc_sweep(peps_ctx* c, uint64_t* S, int n, int nsweeps, uint64_t
   g_err.clear();
   if (c->elem == 8) return mc_impl<double>(c, S, n, nsweeps, seed, chain0, sweep0, accepted);
   return mc_impl<float>(c, S, n, nsweeps, seed, chain0, sweep0, accepted);
+}
+
+peps_status peps_correlations(peps_ctx* c, const uint64_t* S, int n, const int* sites_host, int nc, double* m2_dev,
+                              double* corr_dev, int32_t* status_dev) {
+  peps_status st = check_ctx(c, S, n);
+  if (st != PEPS_OK) return st;
+  if (nc < 1 || !sites_host) return fail(PEPS_EINVAL, "need at least one central site");
+  std::vector<char> seen(c->g.N, 0);
+  for (int p = 0; p < nc; ++p) {
+    if (sites_host[p] < 0 || sites_host[p] >= c->g.N || seen[sites_host[p]])
+      return fail(PEPS_EINVAL, "central sites must be distinct sites of the lattice");
+    seen[sites_host[p]] = 1;
+  }
+  g_err.clear();
+  if (n == 0) return PEPS_OK;
+  if (c->elem == 8) return correlations_impl<double>(c, S, n, sites_host, nc, m2_dev, corr_dev, status_dev);
+  return correlations_impl<float>(c, S, n, sites_host, nc, m2_dev, corr_dev, status_dev);
+}
+
+peps_status peps_set_env_cache(peps_ctx* c, int on) {
+  if (!c) return fail(PEPS_EINVAL, "null context");
+  c->env_cache = on != 0;
+  c->cache_dirty = true;
+  return PEPS_OK;
+}
+
+peps_status peps_set_graphs(peps_ctx* c, int on) {
+  if (!c) return fail(PEPS_EINVAL, "null context");
+  if (on && !c->stream) return fail(PEPS_EINVAL, "graph capture needs a context created on a non-default stream");
+  if (!on) drop_graphs(c);
+  c->graphs = on != 0;
+  return PEPS_OK;
+}
+
+peps_status peps_graph_stats(peps_ctx* c, long long* stats) {
+  if (!c || !stats) return fail(PEPS_EINVAL, "null argument");
+  stats[0] = (long long)c->gcache.size();
+  stats[1] = c->graph_captures;
+  stats[2] = c->graph_replays;
+  return PEPS_OK;
+}
+
+peps_status peps_tuned_config(peps_ctx* c, int* vals, double* workspace_gb) {
+  if (!c) return fail(PEPS_EINVAL, "null context");
+  if (vals) {
+    const bool fused = c->elem == 8 ? max_blocks_pair_fused<double>(c->g) > 0 : max_blocks_pair_fused<float>(c->g) > 0;
+    vals[0] = c->pair_tc && c->pair_mode == 0 ? 0 : ((c->pair_mode == 2 || !fused) ? 2 : 1);
+    vals[1] = c->row_generic;
+    vals[2] = c->boundary_ctas > 0 ? std::min(c->boundary_ctas, c->res_boundary) : c->res_boundary;
+    vals[3] = c->chunk;
+  }
+  if (workspace_gb) *workspace_gb = c->p.workspace_gb > 0 ? c->p.workspace_gb : 24.0;
+  return PEPS_OK;
+}
+
+peps_status peps_autotune(peps_ctx* c, const uint64_t* S, int n, char* report, size_t report_len) {
+  peps_status st = check_ctx(c, S, n);
+  if (st != PEPS_OK) return st;
+  if (n == 0) return fail(PEPS_EINVAL, "empty probe batch");
+  if (c->parent) return fail(PEPS_EINVAL, "tune the model's context, not a serving worker");
+  g_err.clear();
+  drop_graphs(c);
+  const bool graphs = c->graphs;
+  c->graphs = false;
+  std::string rep;
+  cudaEvent_t e0, e1;
+  PEPS_CUDA(cudaEventCreate(&e0));
+  PEPS_CUDA(cudaEventCreate(&e1));
+  // one untimed and one timed gradient pass over the probe batch
+  auto trial = [&](double& ms) -> peps_status {
+    for (int k = 0; k < 2; ++k) {
+      PEPS_CUDA(cudaEventRecord(e0, c->stream));
+      peps_status s2 = c->elem == 8
+                           ? gradient_impl<double>(c, S, n, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
+                                                   nullptr, nullptr)
+                           : gradient_impl<float>(c, S, n, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
+                                                  nullptr, nullptr);
+      if (s2 != PEPS_OK) return s2;
+      PEPS_CUDA(cudaEventRecord(e1, c->stream));
+      PEPS_CUDA(cudaEventSynchronize(e1));
+      float t = 0.f;
+      PEPS_CUDA(cudaEventElapsedTime(&t, e0, e1));
+      ms = t;
+    }
+    return PEPS_OK;
+  };
+  char buf[160];
+  auto pick = [&](const char* what, std::vector<int> cands, std::function<void(int)> set,
+                  std::function<const char*(int)> name) -> peps_status {
+    double best = 1e300;
+    int bi = cands[0];
+    rep += what;
+    rep += ":";
+    for (int v : cands) {
+      set(v);
+      double ms = 0;
+      peps_status s2 = trial(ms);
+      if (s2 != PEPS_OK) return s2;
+      snprintf(buf, sizeof(buf), " %s %.1f ms", name(v), ms);
+      rep += buf;
+      if (ms < best) {
+        best = ms;
+        bi = v;
+      }
+    }
+    set(bi);
+    snprintf(buf, sizeof(buf), " -> %s; ", name(bi));
+    rep += buf;
+    return PEPS_OK;
+  };
+  const bool fp64 = c->elem == 8;
+  const bool fused_pair = fp64 ? max_blocks_pair_fused<double>(c->g) > 0 : max_blocks_pair_fused<float>(c->g) > 0;
+  std::vector<int> pc;
+  if (c->pair_tc) pc.push_back(0);
+  if (fused_pair) pc.push_back(1);
+  pc.push_back(2);
+  static const char* pnames[] = {"tensor-core", "fused", "generic"};
+  static const char* rnames[] = {"fused", "generic"};
+  if (c->g.Ly > 1 && pc.size() > 1)
+    st = pick("two-row kernel", pc, [&](int v) { c->pair_mode = v == 1 && !c->pair_tc ? 0 : v; apply_variants(c); },
+              [&](int v) { return pnames[v]; });
+  if (st == PEPS_OK)
+    st = pick("single-row kernel", {0, 1}, [&](int v) { c->row_generic = v; apply_variants(c); },
+              [&](int v) { return rnames[v]; });
+  std::vector<std::string> bnames;
+  if (st == PEPS_OK) {
+    std::vector<int> bc = {c->res_boundary};
+    if (c->res_boundary / 2 >= c->nsm) bc.push_back(c->res_boundary / 2);
+    for (int v : bc) bnames.push_back(std::to_string(v) + " CTAs");
+    std::vector<int> idx;
+    for (size_t i = 0; i < bc.size(); ++i) idx.push_back((int)i);
+    st = pick("boundary grid", idx, [&](int i) { c->boundary_ctas = bc[i]; },
+              [&](int i) { return bnames[i].c_str(); });
+  }
+  if (st == PEPS_OK) {
+    // a larger workspace budget means fewer chunks (fewer partial last waves)
+    const double cur = c->p.workspace_gb > 0 ? c->p.workspace_gb : 24.0;
+    size_t freeb = 0, totb = 0;
+    cudaMemGetInfo(&freeb, &totb);
+    const double cap = 0.6 * (double)(freeb + ctx_workspace_bytes(c)) / 1e9;
+    std::vector<double> ws = {cur};
+    for (double f : {2.0, 4.0})
+      if (cur * f <= cap) ws.push_back(cur * f);
+    const size_t per = env_bytes_per_cfg(c) + (size_t)c->g.N * c->g.D * c->g.D * c->g.D * c->g.D * c->elem;
+    if ((double)n * per > cur * 1e9 && ws.size() > 1) {
+      std::vector<std::string> wn;
+      for (double w : ws) wn.push_back(std::to_string((int)w) + " GB");
+      std::vector<int> idx;
+      for (size_t i = 0; i < ws.size(); ++i) idx.push_back((int)i);
+      st = pick("workspace", idx, [&](int i) { c->p.workspace_gb = ws[i]; },
+                [&](int i) { return wn[i].c_str(); });
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->graphs = graphs;
+  if (st != PEPS_OK) return st;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    TuneVal v{c->row_generic, c->pair_mode, c->boundary_ctas, c->p.workspace_gb};
+    bool found = false;
+    for (auto& kv : g_tuned)
+      if (kv.first == tune_key(c)) {
+        kv.second = v;
+        found = true;
+      }
+    if (!found) g_tuned.push_back({tune_key(c), v});
+  }
+  if (report && report_len) {
+    strncpy(report, rep.c_str(), report_len - 1);
+    report[report_len - 1] = 0;
+  }
+  return PEPS_OK;
+}
+
+peps_status peps_packer_create(void* stream, peps_packer** out) {
+  if (!out) return fail(PEPS_EINVAL, "null argument");
+  peps_packer* pk = new peps_packer();
+  pk->stream = (cudaStream_t)stream;
+  *out = pk;
+  return PEPS_OK;
+}
+
+peps_status peps_packer_destroy(peps_packer* pk) {
+  if (!pk) return PEPS_OK;
+  if (pk->stream) cudaStreamSynchronize(pk->stream);
+  else cudaDeviceSynchronize();
+  pk->scratch.release();
+  pk->models.release();
+  pk->start.release();
+  delete pk;
+  return PEPS_OK;
+}
+
+peps_status peps_packer_evaluate(peps_packer* pk, int nreq, peps_ctx* const* ctxs, const uint64_t* const* S,
+                                 const int* n, double* const* logabs, int8_t* const* sign, double* const* eloc,
+                                 void* const* O, int32_t* const* status) {
+  if (!pk || nreq < 0 || (nreq > 0 && (!ctxs || !S || !n))) return fail(PEPS_EINVAL, "null argument");
+  if (nreq == 0) return PEPS_OK;
+  g_err.clear();
+  const size_t elem = ctxs[0] ? ctxs[0]->elem : 0;
+  for (int i = 0; i < nreq; ++i) {
+    if (!ctxs[i]) return fail(PEPS_EINVAL, "null context");
+    if (ctxs[i]->elem != elem) return fail(PEPS_EINVAL, "packed requests must share the precision class (FP64 or FP32)");
+    if (n[i] <= 0 || !S[i]) return fail(PEPS_EINVAL, "every packed request needs configurations");
+    for (int j = 0; j < i; ++j)
+      if (ctxs[j] == ctxs[i]) return fail(PEPS_EINVAL, "a context may appear once per packed launch");
+  }
+  if (elem == 8) return packed_impl<double>(pk, nreq, ctxs, S, n, logabs, sign, eloc, O, status);
+  return packed_impl<float>(pk, nreq, ctxs, S, n, logabs, sign, eloc, O, status);
 }
 
 peps_status peps_profile_enable(peps_ctx* c, int on) {

@@ -72,76 +72,152 @@ size_t mc_slot_elems(const Geometry& g, bool wm_in_smem) {
 }
 
 // ------------------------------------------------------------ k_boundary
+// One work item: the top-down (dir 0) or bottom-up (dir 1) boundary sweep of
+// configuration cfg.  The upper environments U_r go to envU (the last row's
+// MPS to `lastbuf`, then closed to psi), the lower ones L_r to envL.
+template <typename R>
+__device__ void boundary_item(const KArgs<R>& a, int cfg, int dir, R* lastbuf, ZipBufs<R>& zb, R* red,
+                              uint64_t* sp, const int* ones) {
+  const Geometry& g = a.g;
+  const int Lx = g.Lx, Ly = g.Ly, Dc = g.Dc, D = g.D;
+  const size_t envT = (size_t)Dc * D * Dc;
+  if (a.cache) {
+    // this sweep of this configuration is already in place (same bits, same
+    // tensors, same workspace): its outputs were kept, only its flag is raised again
+    const unsigned bits = a.cache[cfg];
+    if (bits & (1u << dir)) {
+      if ((bits & (4u << dir)) && threadIdx.x == 0) atomicOr(&a.flags[cfg], kFlagZeroW);
+      return;
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < g.nwords; i += blockDim.x) sp[i] = a.S[(size_t)cfg * g.nwords + i];
+  __syncthreads();
+  const R* Min = a.triv_mps;
+  double ls = 0.0;
+  bool zero = false;
+  for (int j = 0; j < Ly; ++j) {
+    const int r = dir == 0 ? j : Ly - 1 - j;
+    if (dir == 1 && r == 0) break;
+    R* Mout;
+    if (dir == 0) Mout = r <= Ly - 2 ? a.envU + ((size_t)cfg * Ly + r) * Lx * envT : lastbuf;
+    else Mout = a.envL + ((size_t)cfg * Ly + r) * Lx * envT;
+    const int* bdin = j == 0 ? ones : a.bd + ((size_t)dir * Ly + (j - 1)) * (Lx + 1);
+    const double nrm = absorb_row<R>(a, Min, Mout, r, dir, (j % 2) == 0, bdin, sp, zb, red);
+    if (!(nrm > 0.0)) zero = true;
+    else ls += log(nrm);
+    if (dir == 0 && a.lnU && threadIdx.x == 0) a.lnU[(size_t)cfg * Ly + r] = nrm > 0.0 ? log(nrm) : -INFINITY;
+    Min = Mout;
+  }
+  if (dir == 0) {
+    // All physical legs are one now: close the chain of matrices M_c[:, 0, :].
+    __shared__ R vec[kMaxDc], nv[kMaxDc];
+    if (threadIdx.x == 0) {
+      const int* bdl = a.bd + ((size_t)0 * Ly + (Ly - 1)) * (Lx + 1);
+      vec[0] = R(1);
+      int na = 1;
+      for (int c = 0; c < Lx; ++c) {
+        const int nb = bdl[c + 1];
+        const R* M = lastbuf + (size_t)c * envT;
+        for (int b = 0; b < nb; ++b) {
+          R s = R(0);
+          for (int x = 0; x < na; ++x) s += vec[x] * M[(size_t)x * D * Dc + b];
+          nv[b] = s;
+        }
+        for (int b = 0; b < nb; ++b) vec[b] = nv[b];
+        na = nb;
+      }
+      const R v = vec[0];
+      if (zero || v == R(0)) {
+        a.logabs[cfg] = -INFINITY;
+        a.sign[cfg] = 0;
+        atomicOr(&a.flags[cfg], kFlagZeroW);
+      } else {
+        a.logabs[cfg] = ls + log(fabs((double)v));
+        a.sign[cfg] = v > R(0) ? 1 : -1;
+      }
+    }
+  } else if (zero && threadIdx.x == 0) {
+    atomicOr(&a.flags[cfg], kFlagZeroW);
+  }
+  if (a.cache && threadIdx.x == 0) atomicOr(&a.cache[cfg], (1u << dir) | (zero ? (4u << dir) : 0u));
+}
+
+__global__ void k_cache_check(const uint64_t* S, uint64_t* Scache, unsigned* bits, int n, int nwords) {
+  for (int cfg = blockIdx.x * blockDim.x + threadIdx.x; cfg < n; cfg += gridDim.x * blockDim.x) {
+    bool same = true;
+    for (int w = 0; w < nwords; ++w) same = same && S[(size_t)cfg * nwords + w] == Scache[(size_t)cfg * nwords + w];
+    if (!same) {
+      bits[cfg] = 0u;
+      for (int w = 0; w < nwords; ++w) Scache[(size_t)cfg * nwords + w] = S[(size_t)cfg * nwords + w];
+    }
+  }
+}
+
+cudaError_t launch_cache_check(const uint64_t* S, uint64_t* Scache, unsigned* bits, int n, int nwords,
+                               cudaStream_t st) {
+  k_cache_check<<<(n + 127) / 128, 128, 0, st>>>(S, Scache, bits, n, nwords);
+  return cudaGetLastError();
+}
+
 template <typename R>
 __global__ void __launch_bounds__(kThreads) k_boundary(KArgs<R> a, int dirs) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ R red[64];
   __shared__ uint64_t sp[kMaxWords];
   __shared__ int ones[kMaxDcD + 1];
-  const Geometry& g = a.g;
-  const int Lx = g.Lx, Ly = g.Ly, Dc = g.Dc, D = g.D;
-  const size_t envT = (size_t)Dc * D * Dc;
-  R* p = a.scratch + (size_t)blockIdx.x * a.slot_elems;
-  ZipBufs<R> zb;
   __shared__ double dred[kWarps];
   __shared__ R wv[kMaxDcD];
+  const Geometry& g = a.g;
+  R* p = a.scratch + (size_t)blockIdx.x * a.slot_elems;
+  ZipBufs<R> zb;
   R* gsm;
   int* gism;
   smem_split<R>(smem_raw, g, true, a.smem_wm != 0, gsm, gism);
   carve_zip<R>(g, p, zb, a.smem_wm ? gsm : nullptr, red, dred, wv, gsm, gism);
-  R* lastbuf = p;
-  for (int i = threadIdx.x; i <= Lx; i += blockDim.x) ones[i] = 1;
-  for (int item = blockIdx.x; item < a.n * dirs; item += gridDim.x) {
-    const int cfg = item / dirs, dir = item % dirs;
-    __syncthreads();
-    for (int i = threadIdx.x; i < g.nwords; i += blockDim.x) sp[i] = a.S[(size_t)cfg * g.nwords + i];
-    __syncthreads();
-    const R* Min = a.triv_mps;
-    double ls = 0.0;
-    bool zero = false;
-    for (int j = 0; j < Ly; ++j) {
-      const int r = dir == 0 ? j : Ly - 1 - j;
-      if (dir == 1 && r == 0) break;
-      R* Mout;
-      if (dir == 0) Mout = r <= Ly - 2 ? a.envU + ((size_t)cfg * Ly + r) * Lx * envT : lastbuf;
-      else Mout = a.envL + ((size_t)cfg * Ly + r) * Lx * envT;
-      const int* bdin = j == 0 ? ones : a.bd + ((size_t)dir * Ly + (j - 1)) * (Lx + 1);
-      const double nrm = absorb_row<R>(a, Min, Mout, r, dir, (j % 2) == 0, bdin, sp, zb, red);
-      if (!(nrm > 0.0)) zero = true;
-      else ls += log(nrm);
-      Min = Mout;
+  for (int i = threadIdx.x; i <= g.Lx; i += blockDim.x) ones[i] = 1;
+  for (int item = blockIdx.x; item < a.n * dirs; item += gridDim.x)
+    boundary_item<R>(a, item / dirs, item % dirs, p, zb, red, sp, ones);
+}
+
+// The boundary sweeps of several models (lattices, D, Dc of one precision) in
+// one persistent launch.  Work items are numbered model after model; start[m]
+// is the first item of model m (start[nm] = total), each model contributing
+// n * dirs items.  Every CTA has one scratch slot of slot_elems reals, sized
+// for the largest model, and dynamic shared memory for the largest model; a
+// CTA lays its slot and shared memory out again whenever its next item
+// belongs to another model.  Per configuration the arithmetic is that of
+// k_boundary, so results are bit-identical to separate launches.
+template <typename R>
+__global__ void __launch_bounds__(kThreads) k_boundary_packed(const KArgs<R>* __restrict__ models,
+                                                              const int* __restrict__ start, int nm, int dirs,
+                                                              R* scratch, size_t slot_elems) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ R red[64];
+  __shared__ uint64_t sp[kMaxWords];
+  __shared__ int ones[kMaxDcD + 1];
+  __shared__ double dred[kWarps];
+  __shared__ R wv[kMaxDcD];
+  for (int i = threadIdx.x; i <= kMaxDcD; i += blockDim.x) ones[i] = 1;
+  const int total = start[nm];
+  int cur = -1;
+  ZipBufs<R> zb;
+  R* p = nullptr;
+  for (int item = blockIdx.x; item < total; item += gridDim.x) {
+    int m = cur < 0 ? 0 : cur;
+    while (m + 1 < nm && start[m + 1] <= item) ++m;
+    const KArgs<R>& a = models[m];
+    if (m != cur) {
+      __syncthreads();
+      p = scratch + (size_t)blockIdx.x * slot_elems;
+      R* gsm;
+      int* gism;
+      smem_split<R>(smem_raw, a.g, true, a.smem_wm != 0, gsm, gism);
+      carve_zip<R>(a.g, p, zb, a.smem_wm ? gsm : nullptr, red, dred, wv, gsm, gism);
+      cur = m;
     }
-    if (dir == 0) {
-      // All physical legs are one now: close the chain of matrices M_c[:, 0, :].
-      __shared__ R vec[kMaxDc], nv[kMaxDc];
-      if (threadIdx.x == 0) {
-        const int* bdl = a.bd + ((size_t)0 * Ly + (Ly - 1)) * (Lx + 1);
-        vec[0] = R(1);
-        int na = 1;
-        for (int c = 0; c < Lx; ++c) {
-          const int nb = bdl[c + 1];
-          const R* M = lastbuf + (size_t)c * envT;
-          for (int b = 0; b < nb; ++b) {
-            R s = R(0);
-            for (int x = 0; x < na; ++x) s += vec[x] * M[(size_t)x * D * Dc + b];
-            nv[b] = s;
-          }
-          for (int b = 0; b < nb; ++b) vec[b] = nv[b];
-          na = nb;
-        }
-        const R v = vec[0];
-        if (zero || v == R(0)) {
-          a.logabs[cfg] = -INFINITY;
-          a.sign[cfg] = 0;
-          atomicOr(&a.flags[cfg], kFlagZeroW);
-        } else {
-          a.logabs[cfg] = ls + log(fabs((double)v));
-          a.sign[cfg] = v > R(0) ? 1 : -1;
-        }
-      }
-    } else if (zero && threadIdx.x == 0) {
-      atomicOr(&a.flags[cfg], kFlagZeroW);
-    }
+    const int local = item - start[m];
+    boundary_item<R>(a, local / dirs, local % dirs, p, zb, red, sp, ones);
   }
 }
 
@@ -210,32 +286,37 @@ __global__ void k_grad_accum(GradArgs a, const R* __restrict__ O) {
   }
 }
 
-// sums[0] += sum of E over configurations with status 0, sums[1] += their count.
+// Over the configurations with status 0: sums[0] += sum of E, sums[1] += their
+// count, sums[2] += sum of E^2.
 __global__ void k_sum_eloc(const double* eloc, const int* status, int n, double* sums) {
-  __shared__ double sh[2][kThreads];
-  double s = 0, c = 0;
+  __shared__ double sh[3][kThreads];
+  double s = 0, c = 0, q = 0;
   for (int i = threadIdx.x; i < n; i += blockDim.x)
     if (status[i] == 0) {
       s += eloc[i];
       c += 1;
+      q += eloc[i] * eloc[i];
     }
   sh[0][threadIdx.x] = s;
   sh[1][threadIdx.x] = c;
+  sh[2][threadIdx.x] = q;
   __syncthreads();
   for (int o = blockDim.x / 2; o > 0; o >>= 1) {
     if (threadIdx.x < o) {
       sh[0][threadIdx.x] += sh[0][threadIdx.x + o];
       sh[1][threadIdx.x] += sh[1][threadIdx.x + o];
+      sh[2][threadIdx.x] += sh[2][threadIdx.x + o];
     }
     __syncthreads();
   }
   if (threadIdx.x == 0) {
     sums[0] += sh[0][0];
     sums[1] += sh[1][0];
+    sums[2] += sh[2][0];
   }
 }
 
-// grad = 2 (<E O> - <E><O>), cov = grad / 2.
+// grad = 2 (<E O> - <E><O>), cov = grad / 2 (Sec. II), from the sums.
 __global__ void k_grad_finalize(int total, const double* sums, const double* sumO, const double* sumEO, double* grad,
                                 double* cov) {
   const double n = sums[1];
@@ -391,7 +472,29 @@ cudaError_t launch_grad_finalize(int total, int, const double* sums, const doubl
   return cudaGetLastError();
 }
 
+template <typename R>
+int max_blocks_boundary_packed(size_t smem) {
+  int dev = 0, nsm = 0, nb = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  prefer_shared(k_boundary_packed<R>, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_boundary_packed<R>, kThreads, smem);
+  return nsm * (nb < 1 ? 1 : nb);
+}
+
+template <typename R>
+cudaError_t launch_boundary_packed(const KArgs<R>* models_dev, const int* start_dev, int nm, int dirs, R* scratch,
+                                   size_t slot_elems, size_t smem, int grid, cudaStream_t st) {
+  cudaError_t e = prefer_shared(k_boundary_packed<R>, smem);
+  if (e != cudaSuccess) return e;
+  k_boundary_packed<R><<<grid, kThreads, smem, st>>>(models_dev, start_dev, nm, dirs, scratch, slot_elems);
+  return cudaGetLastError();
+}
+
 #define PEPS_INST(R)                                                                                    \
+  template int max_blocks_boundary_packed<R>(size_t);                                                   \
+  template cudaError_t launch_boundary_packed<R>(const KArgs<R>*, const int*, int, int, R*, size_t, size_t, \
+                                                 int, cudaStream_t);                                    \
   template int max_blocks_boundary<R>(const Geometry&);                                                 \
   template cudaError_t launch_boundary<R>(const KArgs<R>&, int, int, cudaStream_t);                     \
   template cudaError_t launch_grad_accum<R>(const GradArgs&, const R*, cudaStream_t);

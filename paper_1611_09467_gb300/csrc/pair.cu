@@ -408,8 +408,8 @@ cudaError_t launch_pair_tc(const KArgs<float>& a, int grid, cudaStream_t st) {
 }
 
 template <typename R>
-cudaError_t launch_pair(const KArgs<R>& a, int grid, cudaStream_t st) {
-  switch (pair_fused_id<R>(a.g)) {
+cudaError_t launch_pair(const KArgs<R>& a, int grid, cudaStream_t st, int generic) {
+  switch (generic ? 0 : pair_fused_id<R>(a.g)) {
     case 1: return launch_pair_fused<R, 2, 4>(a, grid, st);
     case 2: return launch_pair_fused<R, 4, 8>(a, grid, st);
     case 3: return launch_pair_fused<R, sizeof(R) == 4 ? 6 : 2, sizeof(R) == 4 ? 12 : 4>(a, grid, st);
@@ -425,7 +425,7 @@ cudaError_t launch_pair(const KArgs<R>& a, int grid, cudaStream_t st) {
 #define PEPS_INST(R)                                                                                    \
   template int max_blocks_pair<R>(const Geometry&);                                                     \
   template int max_blocks_pair_fused<R>(const Geometry&);                                               \
-  template cudaError_t launch_pair<R>(const KArgs<R>&, int, cudaStream_t);
+  template cudaError_t launch_pair<R>(const KArgs<R>&, int, cudaStream_t, int);
 PEPS_INST(double)
 PEPS_INST(float)
 

@@ -81,7 +81,7 @@ __global__ void __launch_bounds__(kThreads) k_row(KArgs<R> a) {
     }
     if (threadIdx.x == 0) {
       a.eloc_h[(size_t)cfg * Ly + r] = eh;
-      a.w_row[(size_t)cfg * Ly + r] = (double)W;
+      a.w_row[(size_t)cfg * Ly + r] = ldexp((double)W, eG[0]);
       if (!ok) atomicOr(&a.flags[cfg], kFlagZeroW);
     }
   }
@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(kThreads) k_row_fused(KArgs<R> a) {
     }
     if (threadIdx.x == 0) {
       a.eloc_h[(size_t)cfg * Ly + r] = eh;
-      a.w_row[(size_t)cfg * Ly + r] = (double)W;
+      a.w_row[(size_t)cfg * Ly + r] = ldexp((double)W, eG[0]);
       if (!ok) atomicOr(&a.flags[cfg], kFlagZeroW);
     }
   }
@@ -192,8 +192,8 @@ static cudaError_t launch_row_fused(const KArgs<R>& a, int grid, cudaStream_t st
 }
 
 template <typename R>
-int max_blocks_row(const Geometry& g) {
-  switch (row_fused_id<R>(g)) {
+int max_blocks_row(const Geometry& g, int generic) {
+  switch (generic ? 0 : row_fused_id<R>(g)) {
     case 1: return row_fused_blocks<R, 2, 4>();
     case 2: return row_fused_blocks<R, 4, 8>();
     case 3: return row_fused_blocks<R, 6, 12>();
@@ -209,8 +209,8 @@ int max_blocks_row(const Geometry& g) {
 }
 
 template <typename R>
-cudaError_t launch_row(const KArgs<R>& a, int grid, cudaStream_t st) {
-  switch (row_fused_id<R>(a.g)) {
+cudaError_t launch_row(const KArgs<R>& a, int grid, cudaStream_t st, int generic) {
+  switch (generic ? 0 : row_fused_id<R>(a.g)) {
     case 1: return launch_row_fused<R, 2, 4>(a, grid, st);
     case 2: return launch_row_fused<R, 4, 8>(a, grid, st);
     case 3: return launch_row_fused<R, 6, 12>(a, grid, st);
@@ -224,8 +224,8 @@ cudaError_t launch_row(const KArgs<R>& a, int grid, cudaStream_t st) {
 }
 
 #define PEPS_INST(R)                                                                                    \
-  template int max_blocks_row<R>(const Geometry&);                                                      \
-  template cudaError_t launch_row<R>(const KArgs<R>&, int, cudaStream_t);
+  template int max_blocks_row<R>(const Geometry&, int);                                                 \
+  template cudaError_t launch_row<R>(const KArgs<R>&, int, cudaStream_t, int);
 PEPS_INST(double)
 PEPS_INST(float)
 

@@ -43,15 +43,26 @@ struct Request {
   void* O;
   int32_t* status;
   Clock::time_point submitted;
+  // chain requests: Metropolis sweeps on S (resident, updated in place) first
+  uint64_t* S_mut = nullptr;
+  int nsweeps = 0;
+  uint64_t seed = 0, chain0 = 0, sweep0 = 0;
+};
+
+struct Worker {
+  peps_ctx* model;
+  peps_ctx* ctx;
+  const uint64_t* last_S;   // configurations whose environments its cache holds
 };
 
 struct Lane {
   cudaStream_t stream = nullptr;
   cudaEvent_t done = nullptr;
   bool busy = false;
-  Request req{};
+  std::vector<Request> reqs;   // the request, or the requests packed into one launch
   // worker contexts of this lane, one per model, least recently used first
-  std::vector<std::pair<peps_ctx*, peps_ctx*>> workers;
+  std::vector<Worker> workers;
+  peps_packer* packer = nullptr;
 };
 
 }  // namespace
@@ -66,6 +77,7 @@ struct peps_server {
   std::vector<double> latency_ms;
   std::deque<std::pair<long long, double>> finished;   // retired, not yet reported by poll
   size_t peak_bytes = 0;
+  int pack_max = 0, pack_width = 1;   // packing of small requests (peps_server_set_packing)
 };
 
 namespace {
@@ -73,13 +85,13 @@ namespace {
 size_t in_use(const peps_server* s) {
   size_t b = 0;
   for (const Lane& l : s->lanes)
-    for (const auto& w : l.workers) b += peps::ctx_workspace_bytes(w.second);
+    for (const auto& w : l.workers) b += peps::ctx_workspace_bytes(w.ctx);
   return b;
 }
 
 int find_worker(const Lane& l, const peps_ctx* model) {
   for (size_t k = 0; k < l.workers.size(); ++k)
-    if (l.workers[k].first == model) return (int)k;
+    if (l.workers[k].model == model) return (int)k;
   return -1;
 }
 
@@ -88,7 +100,7 @@ size_t extra_bytes(const peps_server* s, const Lane& l, const Request& r) {
   const size_t need = peps::ctx_footprint(r.model, r.n, s->lane_gb, (int)s->lanes.size());
   const int k = find_worker(l, r.model);
   if (k >= 0) {
-    const size_t have = peps::ctx_workspace_bytes(l.workers[k].second);
+    const size_t have = peps::ctx_workspace_bytes(l.workers[k].ctx);
     return need > have ? need - have : 0;
   }
   return need;
@@ -104,7 +116,7 @@ bool make_room(peps_server* s, size_t extra, const peps_ctx* keep) {
     for (Lane& l : s->lanes) {
       if (l.busy) continue;
       for (const auto& w : l.workers)
-        if (w.second != keep) {
+        if (w.ctx != keep) {
           victim_lane = &l;
           break;
         }
@@ -112,9 +124,9 @@ bool make_room(peps_server* s, size_t extra, const peps_ctx* keep) {
     }
     if (!victim_lane) return false;
     for (auto it = victim_lane->workers.begin(); it != victim_lane->workers.end(); ++it)
-      if (it->second != keep) {
+      if (it->ctx != keep) {
         cudaStreamSynchronize(victim_lane->stream);
-        peps_destroy(it->second);
+        peps_destroy(it->ctx);
         victim_lane->workers.erase(it);
         break;
       }
@@ -122,27 +134,83 @@ bool make_room(peps_server* s, size_t extra, const peps_ctx* keep) {
   return true;
 }
 
-peps_status launch(peps_server* s, Lane& l, const Request& r) {
-  int k = find_worker(l, r.model);
+// The lane's worker of a model (created on first use; most recently used last).
+peps_ctx* worker_for(peps_server* s, Lane& l, peps_ctx* model, Worker** wout) {
+  int k = find_worker(l, model);
   if (k < 0) {
-    peps_ctx* w = peps::ctx_clone(r.model, l.stream, s->lane_gb, (int)s->lanes.size());
-    if (!w) return PEPS_ENOMEM;
-    l.workers.emplace_back(r.model, w);
+    peps_ctx* w = peps::ctx_clone(model, l.stream, s->lane_gb, (int)s->lanes.size());
+    if (!w) return nullptr;
+    peps_set_env_cache(w, 1);
+    l.workers.push_back({model, w, nullptr});
     k = (int)l.workers.size() - 1;
   } else if (k != (int)l.workers.size() - 1) {
-    const auto w = l.workers[k];   // most recently used goes last
+    const Worker w = l.workers[k];
     l.workers.erase(l.workers.begin() + k);
     l.workers.push_back(w);
     k = (int)l.workers.size() - 1;
   }
-  peps_ctx* worker = l.workers[k].second;
+  *wout = &l.workers[k];
+  return l.workers[k].ctx;
+}
+
+peps_status launch(peps_server* s, Lane& l, const Request& r) {
+  Worker* wk = nullptr;
+  peps_ctx* worker = worker_for(s, l, r.model, &wk);
+  if (!worker) return PEPS_ENOMEM;
+  if (r.nsweeps > 0) {
+    const peps_status st = peps_mc_sweep(worker, r.S_mut, r.n, r.nsweeps, r.seed, r.chain0, r.sweep0, nullptr);
+    if (st != PEPS_OK) return st;
+  }
   const peps_status st = peps_evaluate(worker, r.S, r.n, r.logabs, r.sign, r.eloc, r.O, r.status);
   if (st != PEPS_OK) return st;
+  wk->last_S = r.S;
   if (cudaEventRecord(l.done, l.stream) != cudaSuccess) return PEPS_ECUDA;
   l.busy = true;
-  l.req = r;
+  l.reqs.assign(1, r);
   s->peak_bytes = std::max(s->peak_bytes, in_use(s));
   return PEPS_OK;
+}
+
+// Several small requests of distinct models (one precision class) in one
+// packed launch on the lane: their boundary sweeps share one kernel.
+peps_status launch_packed(peps_server* s, Lane& l, const std::vector<Request>& rs) {
+  if (!l.packer) {
+    const peps_status st = peps_packer_create(l.stream, &l.packer);
+    if (st != PEPS_OK) return st;
+  }
+  const int k = (int)rs.size();
+  std::vector<peps_ctx*> ctxs(k);
+  std::vector<const uint64_t*> S(k);
+  std::vector<int> n(k);
+  std::vector<double*> la(k), el(k);
+  std::vector<int8_t*> sg(k);
+  std::vector<void*> O(k);
+  std::vector<int32_t*> st(k);
+  for (int i = 0; i < k; ++i) {
+    Worker* wk = nullptr;
+    ctxs[i] = worker_for(s, l, rs[i].model, &wk);
+    if (!ctxs[i]) return PEPS_ENOMEM;
+    wk->last_S = nullptr;   // the packed launch bypasses the worker's cache
+    S[i] = rs[i].S;
+    n[i] = rs[i].n;
+    la[i] = rs[i].logabs;
+    sg[i] = rs[i].sign;
+    el[i] = rs[i].eloc;
+    O[i] = rs[i].O;
+    st[i] = rs[i].status;
+  }
+  const peps_status r = peps_packer_evaluate(l.packer, k, ctxs.data(), S.data(), n.data(), la.data(), sg.data(),
+                                             el.data(), O.data(), st.data());
+  if (r != PEPS_OK) return r;
+  if (cudaEventRecord(l.done, l.stream) != cudaSuccess) return PEPS_ECUDA;
+  l.busy = true;
+  l.reqs = rs;
+  s->peak_bytes = std::max(s->peak_bytes, in_use(s));
+  return PEPS_OK;
+}
+
+bool packable(const peps_server* s, const Request& r) {
+  return s->pack_max > 0 && r.nsweeps == 0 && r.n <= s->pack_max;
 }
 
 // Retires finished lanes, then admits queued requests that fit.
@@ -152,34 +220,76 @@ peps_status step(peps_server* s) {
     const cudaError_t q = cudaEventQuery(l.done);
     if (q == cudaErrorNotReady) continue;
     if (q != cudaSuccess) return PEPS_ECUDA;
-    const double ms = std::chrono::duration<double, std::milli>(Clock::now() - l.req.submitted).count();
     l.busy = false;
-    s->completed += 1;
-    s->latency_ms.push_back(ms);
-    s->finished.emplace_back(l.req.id, ms);
+    for (const Request& r : l.reqs) {
+      const double ms = std::chrono::duration<double, std::milli>(Clock::now() - r.submitted).count();
+      s->completed += 1;
+      s->latency_ms.push_back(ms);
+      s->finished.emplace_back(r.id, ms);
+    }
+    l.reqs.clear();
   }
   for (auto it = s->queue.begin(); it != s->queue.end();) {
     Lane* free_lane = nullptr;
-    // prefer a free lane that already holds a worker of this model
+    // prefer a free lane whose worker of this model last held these
+    // configurations (its environment cache), then one with a worker of the model
+    auto score = [&](const Lane& l) {
+      const int k = find_worker(l, it->model);
+      if (k < 0) return 0;
+      return l.workers[k].last_S == it->S ? 2 : 1;
+    };
     for (Lane& l : s->lanes)
-      if (!l.busy && (!free_lane || (find_worker(l, it->model) >= 0 && find_worker(*free_lane, it->model) < 0)))
-        free_lane = &l;
+      if (!l.busy && (!free_lane || score(l) > score(*free_lane))) free_lane = &l;
     if (!free_lane) break;
     const size_t extra = extra_bytes(s, *free_lane, *it);
     const int k = find_worker(*free_lane, it->model);
-    if (!make_room(s, extra, k >= 0 ? free_lane->workers[k].second : nullptr)) {
+    if (!make_room(s, extra, k >= 0 ? free_lane->workers[k].ctx : nullptr)) {
       ++it;   // does not fit now: let a smaller queued request pass
       continue;
     }
-    if (launch(s, *free_lane, *it) != PEPS_OK) {
+    // co-admit other small queued requests of distinct models and the same
+    // precision class into one packed launch
+    std::vector<std::deque<Request>::iterator> group;
+    if (packable(s, *it)) {
+      group.push_back(it);
+      size_t grown = extra;
+      for (auto jt = std::next(it); jt != s->queue.end() && (int)group.size() < s->pack_width; ++jt) {
+        if (!packable(s, *jt) || peps::ctx_is_fp64(jt->model) != peps::ctx_is_fp64(it->model)) continue;
+        bool dup = false;
+        for (auto& g : group) dup = dup || g->model == jt->model;
+        if (dup) continue;
+        const size_t e2 = extra_bytes(s, *free_lane, *jt);
+        if (in_use(s) + grown + e2 > s->budget) continue;
+        grown += e2;
+        group.push_back(jt);
+      }
+    }
+    peps_status st;
+    if (group.size() > 1) {
+      std::vector<Request> rs;
+      for (auto& g : group) rs.push_back(*g);
+      st = launch_packed(s, *free_lane, rs);
+    } else {
+      st = launch(s, *free_lane, *it);
+      group.assign(1, it);
+    }
+    if (st != PEPS_OK) {
       // The request cannot run (its workspace does not fit in device memory,
       // or a launch failed).  It is retired as failed, with a negative
       // latency, so that the queue keeps moving; peps_last_error holds why.
-      s->finished.emplace_back(it->id, -1.0);
-      it = s->queue.erase(it);
-      continue;
+      for (auto& g : group) s->finished.emplace_back(g->id, -1.0);
     }
-    it = s->queue.erase(it);
+    // remove the group from the queue (erasing inside a deque invalidates
+    // its iterators, so the scan starts again; every admission occupies a
+    // lane, so this ends once the lanes are busy or nothing more fits)
+    std::vector<long long> ids;
+    for (auto& g : group) ids.push_back(g->id);
+    s->queue.erase(std::remove_if(s->queue.begin(), s->queue.end(),
+                                  [&](const Request& q) {
+                                    return std::find(ids.begin(), ids.end(), q.id) != ids.end();
+                                  }),
+                   s->queue.end());
+    it = s->queue.begin();
   }
   return PEPS_OK;
 }
@@ -222,8 +332,9 @@ peps_status peps_server_destroy(peps_server* s) {
   if (!s) return PEPS_OK;
   for (Lane& l : s->lanes) {
     if (l.stream) cudaStreamSynchronize(l.stream);
-    for (auto& w : l.workers) peps_destroy(w.second);
+    for (auto& w : l.workers) peps_destroy(w.ctx);
     l.workers.clear();
+    if (l.packer) peps_packer_destroy(l.packer);
     if (l.done) cudaEventDestroy(l.done);
     if (l.stream) cudaStreamDestroy(l.stream);
   }
@@ -243,6 +354,36 @@ peps_status peps_server_submit(peps_server* s, peps_ctx* model, const uint64_t* 
   s->submitted += 1;
   if (id_out) *id_out = r.id;
   return step(s);
+}
+
+peps_status peps_server_submit_chain(peps_server* s, peps_ctx* model, uint64_t* S_dev, int n, int nsweeps,
+                                     uint64_t seed, uint64_t chain0, uint64_t sweep0, double* logabs_dev,
+                                     int8_t* sign_dev, double* eloc_dev, void* O_dev, int32_t* status_dev,
+                                     long long* id_out) {
+  if (!s || !model || n < 1 || !S_dev || nsweeps < 0) {
+    peps::set_last_error("bad chain request");
+    return PEPS_EINVAL;
+  }
+  Request r{s->next_id++, model, S_dev, n, logabs_dev, sign_dev, eloc_dev, O_dev, status_dev, Clock::now()};
+  r.S_mut = S_dev;
+  r.nsweeps = nsweeps;
+  r.seed = seed;
+  r.chain0 = chain0;
+  r.sweep0 = sweep0;
+  s->queue.push_back(r);
+  s->submitted += 1;
+  if (id_out) *id_out = r.id;
+  return step(s);
+}
+
+peps_status peps_server_set_packing(peps_server* s, int max_configs, int max_requests) {
+  if (!s || max_configs < 0 || max_requests < 1 || max_requests > 64) {
+    peps::set_last_error("need max_configs >= 0 and 1 <= max_requests <= 64");
+    return PEPS_EINVAL;
+  }
+  s->pack_max = max_configs;
+  s->pack_width = max_requests;
+  return PEPS_OK;
 }
 
 peps_status peps_server_poll(peps_server* s, int wait, long long* ids, double* latency_ms, int max, int* ndone) {

@@ -58,6 +58,22 @@ def lib():
         "peps_evaluate": [P, P, i, P, P, P, P, P],
         "peps_gradient": [P, P, i, ctypes.POINTER(d), P, P, P, P, P, P, ctypes.POINTER(i)],
         "peps_mc_sweep": [P, P, i, i, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64, P],
+        "peps_gradient_sums": [P, P, i, P, i, P, P, P, P],
+        "peps_set_graphs": [P, i],
+        "peps_measure_peaks": [P],
+        "peps_set_env_cache": [P, i],
+        "peps_correlations": [P, P, i, P, i, P, P, P],
+        "peps_su_create": [ctypes.POINTER(Params), P, ctypes.POINTER(P)],
+        "peps_su_destroy": [P],
+        "peps_su_evolve": [P, P, P, d, i, ctypes.POINTER(d)],
+        "peps_su_to_peps": [P, P, P, P],
+        "peps_graph_stats": [P, P],
+        "peps_autotune": [P, P, i, ctypes.c_char_p, ctypes.c_size_t],
+        "peps_tuned_config": [P, P, ctypes.POINTER(d)],
+        "peps_packer_create": [P, ctypes.POINTER(P)],
+        "peps_packer_destroy": [P],
+        "peps_packer_evaluate": [P, i, P, P, P, P, P, P, P, P],
+        "peps_gradient_finalize": [P, P, ctypes.POINTER(d), ctypes.POINTER(d), P, P, ctypes.POINTER(i)],
         "peps_synchronize": [P],
         "peps_profile_enable": [P, i],
         "peps_profile_read": [P, P, P, i],
@@ -69,6 +85,8 @@ def lib():
         f = getattr(L, name)
         f.argtypes = argt
         f.restype = ctypes.c_int
+    L.peps_gradient_sums_len.argtypes = [P]
+    L.peps_gradient_sums_len.restype = ctypes.c_size_t
     L.peps_status_str.argtypes = [ctypes.c_int]
     L.peps_status_str.restype = ctypes.c_char_p
     L.peps_last_error.argtypes = []
@@ -83,7 +101,13 @@ def exported_symbols():
     names = ["peps_create", "peps_destroy", "peps_set_tensors", "peps_amplitudes", "peps_local_energy",
              "peps_log_derivatives", "peps_evaluate", "peps_gradient", "peps_mc_sweep", "peps_synchronize",
              "peps_status_str", "peps_last_error", "peps_debug_host_op", "peps_debug_host_zip",
-             "peps_profile_enable", "peps_profile_read", "peps_amplitudes_static"]
+             "peps_profile_enable", "peps_profile_read", "peps_amplitudes_static", "peps_go_step",
+             "peps_gradient_sums", "peps_gradient_sums_len", "peps_gradient_finalize", "peps_set_graphs",
+             "peps_graph_stats", "peps_correlations", "peps_set_env_cache", "peps_measure_peaks", "peps_server_create",
+             "peps_server_destroy", "peps_server_submit", "peps_server_submit_chain", "peps_server_set_packing",
+             "peps_server_poll", "peps_server_stats", "peps_su_create", "peps_su_destroy", "peps_su_evolve", "peps_su_to_peps",
+             "peps_autotune", "peps_tuned_config", "peps_packer_create", "peps_packer_destroy",
+             "peps_packer_evaluate"]
     return {n: hasattr(L, n) for n in names}
 
 
@@ -118,6 +142,14 @@ def host_zip(lr, D, Dc, dims, C, M, T, out_shape):
     check(lib().peps_debug_host_zip(int(lr), D, Dc, _ptr(dims), _ptr(_f64(C)), _ptr(_f64(M)), _ptr(_f64(T)),
                                     _ptr(out)))
     return out
+
+
+def measure_peaks():
+    """Measured TFLOP/s of the pipes the kernels use on the current GPU:
+    {"fp32_simt", "fp64_simt", "tf32_tcgen05"}."""
+    out = np.zeros(3, dtype=np.float64)
+    check(lib().peps_measure_peaks(_ptr(out)))
+    return dict(fp32_simt=float(out[0]), fp64_simt=float(out[1]), tf32_tcgen05=float(out[2]))
 
 
 def amplitudes_static(A_dev, S, Lx, Ly, D, Dc, prec="fp64"):
@@ -232,27 +264,101 @@ class PEPS:
     def log_derivatives(self, S):
         return self.evaluate(S, logabs=False, eloc=False, O=True)["O"]
 
-    def gradient(self, S, per_config=False):
+    def gradient(self, S, per_config=False, out=None):
+        """Energy per site and gradient over the batch S.  ``out`` (a dict a
+        previous call returned, same batch size) reuses its tensors as the
+        outputs, so repeated calls keep one signature for graph replay."""
         torch = self.torch
         S = self._S(S)
         n = S.shape[0]
         dev = S.device
-        grad = torch.empty((self.N, 2, self.D ** 4), dtype=torch.float64, device=dev)
-        cov = torch.empty_like(grad)
-        la = sg = el = st = None
-        if per_config:
-            la = torch.empty(n, dtype=torch.float64, device=dev)
-            sg = torch.empty(n, dtype=torch.int8, device=dev)
-            el = torch.empty(n, dtype=torch.float64, device=dev)
-            st = torch.empty(n, dtype=torch.int32, device=dev)
+        if out is not None:
+            grad, cov = out["grad"], out["cov"]
+            la, sg, el, st = (out.get(k) for k in ("logabs", "sign", "eloc", "status"))
+        else:
+            grad = torch.empty((self.N, 2, self.D ** 4), dtype=torch.float64, device=dev)
+            cov = torch.empty_like(grad)
+            la = sg = el = st = None
+            if per_config:
+                la = torch.empty(n, dtype=torch.float64, device=dev)
+                sg = torch.empty(n, dtype=torch.int8, device=dev)
+                el = torch.empty(n, dtype=torch.float64, device=dev)
+                st = torch.empty(n, dtype=torch.int32, device=dev)
         e = ctypes.c_double()
         used = ctypes.c_int()
         check(lib().peps_gradient(self.h, _ptr(S), n, ctypes.byref(e), _ptr(grad), _ptr(cov), _ptr(la), _ptr(sg),
                                   _ptr(el), _ptr(st), ctypes.byref(used)))
-        out = dict(energy_per_site=e.value, grad=grad, cov=cov, n_used=used.value)
-        if per_config:
-            out.update(logabs=la, sign=sg, eloc=el, status=st)
-        return out
+        res = dict(energy_per_site=e.value, grad=grad, cov=cov, n_used=used.value)
+        if la is not None:
+            res.update(logabs=la, sign=sg, eloc=el, status=st)
+        return res
+
+    def gradient_sums(self, S, sums=None, accumulate=False):
+        """The additive sums behind gradient() (layout in include/peps.h:
+        sum E, count, sum E^2, 0, sum Delta [N][2][D^4], sum E Delta), as a CUDA
+        float64 tensor; with ``sums`` given and ``accumulate``, added to it."""
+        torch = self.torch
+        S = self._S(S)
+        if sums is None:
+            sums = torch.empty(int(lib().peps_gradient_sums_len(self.h)), dtype=torch.float64, device=S.device)
+        check(lib().peps_gradient_sums(self.h, _ptr(S), S.shape[0], _ptr(sums), 1 if accumulate else 0,
+                                       None, None, None, None))
+        return sums
+
+    def gradient_from_sums(self, sums):
+        """Energy per site, its variance, the gradient 2(<E Delta> - <E><Delta>)
+        and its half from sums (e.g. added over ranks)."""
+        torch = self.torch
+        grad = torch.empty((self.N, 2, self.D ** 4), dtype=torch.float64, device=sums.device)
+        cov = torch.empty_like(grad)
+        e, v = ctypes.c_double(), ctypes.c_double()
+        used = ctypes.c_int()
+        check(lib().peps_gradient_finalize(self.h, _ptr(sums), ctypes.byref(e), ctypes.byref(v), _ptr(grad),
+                                           _ptr(cov), ctypes.byref(used)))
+        return dict(energy_per_site=e.value, energy_var=v.value, grad=grad, cov=cov, n_used=used.value)
+
+    def correlations(self, S, sites, corr=True):
+        """Local M^2 per configuration ([n] float64, NaN where status != 0) and,
+        with ``corr``, the [nc, nc] sums of the local S_p.S_q over the
+        configurations with status 0 (Sec. IV)."""
+        torch = self.torch
+        S = self._S(S)
+        n = S.shape[0]
+        sites = np.ascontiguousarray(sites, dtype=np.int32)
+        m2 = torch.empty(n, dtype=torch.float64, device=S.device)
+        C = torch.empty((len(sites), len(sites)), dtype=torch.float64, device=S.device) if corr else None
+        st = torch.empty(n, dtype=torch.int32, device=S.device)
+        check(lib().peps_correlations(self.h, _ptr(S), n, _ptr(sites), len(sites), _ptr(m2), _ptr(C), _ptr(st)))
+        return dict(m2=m2, corr=C, status=st)
+
+    def set_env_cache(self, on=True):
+        """Keep boundary environments across calls for unchanged configurations."""
+        check(lib().peps_set_env_cache(self.h, 1 if on else 0))
+
+    def set_graphs(self, on=True):
+        """CUDA-graph replay of evaluate/gradient calls with a repeated signature."""
+        check(lib().peps_set_graphs(self.h, 1 if on else 0))
+
+    def graph_stats(self):
+        v = np.zeros(3, dtype=np.int64)
+        check(lib().peps_graph_stats(self.h, _ptr(v)))
+        return dict(cached=int(v[0]), captures=int(v[1]), replays=int(v[2]))
+
+    def autotune(self, S):
+        """Times the kernel variants, grid and workspace on the probe batch S and
+        keeps the fastest; returns the report (every trial and the choice)."""
+        buf = ctypes.create_string_buffer(4096)
+        S = self._S(S)
+        check(lib().peps_autotune(self.h, _ptr(S), S.shape[0], buf, 4096))
+        return buf.value.decode()
+
+    def tuned_config(self):
+        v = np.zeros(4, dtype=np.int32)
+        ws = ctypes.c_double()
+        check(lib().peps_tuned_config(self.h, _ptr(v), ctypes.byref(ws)))
+        return dict(two_row_kernel=["tensor-core", "fused", "generic"][v[0]],
+                    single_row_kernel=["fused", "generic"][v[1]], boundary_ctas=int(v[2]),
+                    configs_per_chunk=int(v[3]), workspace_gb=ws.value)
 
     def mc_sweep(self, S, nsweeps, seed, chain0=0, sweep0=0):
         """In place on S (a CUDA int64 tensor); returns the accepted-move counts."""
@@ -278,3 +384,102 @@ class PEPS:
 
     def synchronize(self):
         check(lib().peps_synchronize(self.h))
+
+
+class Packer:
+    """Packed evaluation of requests of several models (boundary sweeps of all
+    requests in one kernel launch) on the current torch stream."""
+
+    def __init__(self):
+        import torch
+        self.torch = torch
+        h = ctypes.c_void_p()
+        check(lib().peps_packer_create(ctypes.c_void_p(torch.cuda.current_stream().cuda_stream), ctypes.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().peps_packer_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def evaluate(self, requests, eloc=True, O=False):
+        """requests: [(PEPS, S)].  Returns one dict per request as PEPS.evaluate."""
+        torch = self.torch
+        k = len(requests)
+        outs = []
+        arr = lambda t: (ctypes.c_void_p * k)(*t)
+        ctxs, Ss, ns, la, sg, el, Ob, st = [], [], [], [], [], [], [], []
+        for m, S in requests:
+            S = m._S(S)
+            n = S.shape[0]
+            o = dict(S=S, logabs=torch.empty(n, dtype=torch.float64, device=S.device),
+                     sign=torch.empty(n, dtype=torch.int8, device=S.device),
+                     eloc=torch.empty(n, dtype=torch.float64, device=S.device) if eloc else None,
+                     O=torch.empty((n, m.N, m.D ** 4), dtype=m.real, device=S.device) if O else None,
+                     status=torch.empty(n, dtype=torch.int32, device=S.device))
+            outs.append(o)
+            ctxs.append(m.h.value)
+            Ss.append(S.data_ptr())
+            ns.append(n)
+            la.append(o["logabs"].data_ptr())
+            sg.append(o["sign"].data_ptr())
+            el.append(o["eloc"].data_ptr() if eloc else None)
+            Ob.append(o["O"].data_ptr() if O else None)
+            st.append(o["status"].data_ptr())
+        nn = (ctypes.c_int * k)(*ns)
+        check(lib().peps_packer_evaluate(self.h, k, arr(ctxs), arr(Ss), nn, arr(la), arr(sg), arr(el), arr(Ob),
+                                         arr(st)))
+        for o in outs:
+            o.pop("S")
+        return outs
+
+
+class SimpleUpdate:
+    """Simple-update imaginary-time evolution (Sec. III) on the GPU.
+
+    ``Gam`` [N][2][D^4] float64 (the Gamma tensors, padded like A) and ``lam``
+    [nbonds][D] float64 (bond weights; horizontal bonds row-major, then
+    vertical) are held as CUDA tensors in ``self.Gam`` and ``self.lam``."""
+
+    def __init__(self, Gam, lam, Lx, Ly, D, J1=1.0, J2=0.0):
+        import torch
+        self.torch = torch
+        self.Lx, self.Ly, self.D, self.N = Lx, Ly, D, Lx * Ly
+        self.Gam = torch.as_tensor(np.ascontiguousarray(Gam, dtype=np.float64)).reshape(self.N, 2, D ** 4).cuda()
+        self.lam = torch.as_tensor(np.ascontiguousarray(lam, dtype=np.float64)).reshape(-1, D).cuda()
+        params = Params(Lx, Ly, 2, D, D, float(J1), float(J2), 0, 0.0)
+        h = ctypes.c_void_p()
+        check(lib().peps_su_create(ctypes.byref(params), ctypes.c_void_p(torch.cuda.current_stream().cuda_stream),
+                                   ctypes.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().peps_su_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def evolve(self, dtau, nsteps, measure=True):
+        """nsteps Trotter steps; returns max|A' - A| / max|A| over the last one
+        (or None without ``measure``)."""
+        c = ctypes.c_double()
+        check(lib().peps_su_evolve(self.h, _ptr(self.Gam), _ptr(self.lam), float(dtau), int(nsteps),
+                                   ctypes.byref(c) if measure else None))
+        return c.value if measure else None
+
+    def to_peps(self):
+        """The PEPS tensors A [N][2][D^4] (CUDA float64, unit norm per site)."""
+        A = self.torch.empty_like(self.Gam)
+        check(lib().peps_su_to_peps(self.h, _ptr(self.Gam), _ptr(self.lam), _ptr(A)))
+        return A

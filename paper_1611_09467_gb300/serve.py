@@ -22,8 +22,12 @@ def _lib():
         L.peps_server_submit.argtypes = [P, P, P, i, P, P, P, P, P, ctypes.POINTER(ctypes.c_longlong)]
         L.peps_server_poll.argtypes = [P, i, P, P, i, ctypes.POINTER(i)]
         L.peps_server_stats.argtypes = [P, P]
+        u64 = ctypes.c_uint64
+        L.peps_server_submit_chain.argtypes = [P, P, P, i, i, u64, u64, u64, P, P, P, P, P,
+                                               ctypes.POINTER(ctypes.c_longlong)]
+        L.peps_server_set_packing.argtypes = [P, i, i]
         for f in ("peps_server_create", "peps_server_destroy", "peps_server_submit", "peps_server_poll",
-                  "peps_server_stats"):
+                  "peps_server_stats", "peps_server_submit_chain", "peps_server_set_packing"):
             getattr(L, f).restype = ctypes.c_int
         L._server_sigs = True
     return L
@@ -66,6 +70,36 @@ class Server:
                                            _p._ptr(out["status"]), ctypes.byref(rid)))
         self.outputs[rid.value] = out
         return rid.value
+
+    def submit_chain(self, model, S, nsweeps, seed, chain0=0, sweep0=0, logabs=True, eloc=True, O=False):
+        """Queues a chain request: S (CUDA int64 [n, words], the chains' state,
+        kept on the device by the caller) takes ``nsweeps`` Metropolis sweeps
+        in place, then is evaluated.  Returns the request id."""
+        torch = self.torch
+        assert isinstance(S, torch.Tensor) and S.is_cuda and S.dtype == torch.int64 and S.is_contiguous()
+        n = S.shape[0]
+        dev = S.device
+        out = dict(
+            S=S,
+            logabs=torch.empty(n, dtype=torch.float64, device=dev) if logabs else None,
+            sign=torch.empty(n, dtype=torch.int8, device=dev) if logabs else None,
+            eloc=torch.empty(n, dtype=torch.float64, device=dev) if eloc else None,
+            O=torch.empty((n, model.N, model.D ** 4), dtype=model.real, device=dev) if O else None,
+            status=torch.empty(n, dtype=torch.int32, device=dev),
+        )
+        torch.cuda.current_stream().synchronize()
+        rid = ctypes.c_longlong()
+        _p.check(_lib().peps_server_submit_chain(self.h, model.h, _p._ptr(S), n, int(nsweeps), int(seed),
+                                                 int(chain0), int(sweep0), _p._ptr(out["logabs"]),
+                                                 _p._ptr(out["sign"]), _p._ptr(out["eloc"]), _p._ptr(out["O"]),
+                                                 _p._ptr(out["status"]), ctypes.byref(rid)))
+        self.outputs[rid.value] = out
+        return rid.value
+
+    def set_packing(self, max_configs, max_requests=8):
+        """Pack co-admitted requests of at most ``max_configs`` configurations
+        (up to ``max_requests`` of distinct models) into one launch; 0 turns it off."""
+        _p.check(_lib().peps_server_set_packing(self.h, int(max_configs), int(max_requests)))
 
     def poll(self, wait=False, max_items=256):
         """[(request id, latency ms)] of requests finished since the last poll."""

@@ -72,7 +72,8 @@ def test_go_step_rejects_a_non_finite_gradient():
         assert torch.equal(before[k], after[k]), k
     # the in-place step without the host copy leaves the same context as with it
     q = PEPS(A, Lx, Ly, D, Dc, J1=1.0, J2=0.5, prec="fp32")
-    gd = torch.from_numpy(g * inputs.edge_mask(Ly, Lx, D).reshape(N, 2, -1)).cuda()
+    mask = np.broadcast_to(inputs.edge_mask(Ly, Lx, D), (N, 2, D, D, D, D)).reshape(N, 2, -1)
+    gd = torch.from_numpy(np.ascontiguousarray(g * mask)).cuda()
     p.go_step(gd, 0.004, seed=1, step=0, copy_back=False)
     A1 = q.go_step(gd, 0.004, seed=1, step=0)
     assert np.array_equal(A1, O.go_step(A, gd.cpu().numpy(), 0.004, 1, 0))
