@@ -199,11 +199,95 @@ def absorb_row(mps, Trow, Dc: int, left_to_right: bool, perturb=None):
     return out, math.log(n)
 
 
+def fit_site(F, Mu, T, G):
+    """P[a', d, b'] = sum F[a,l,a'] Mu[a,u,b] T[l,r,u,d] G[b,r,b']: the
+    derivative of <P|Mu T> with respect to the candidate tensor at one column
+    (its environment in the overlap network)."""
+    X = np.tensordot(F, Mu, axes=([0], [0]))            # [l, a', u, b]
+    X = np.tensordot(X, T, axes=([0, 2], [0, 2]))       # [a', b, r, d]
+    return np.tensordot(X, G, axes=([1, 2], [0, 1]))   # [a', d, b']
+
+
+def absorb_row_fit(mps, Trow, Dc, left_to_right, sweeps):
+    """Absorb one row with the variational-fit truncation (the boundary-MPS
+    method of Sec. II by variational compression): start from the zip-up
+    result of `absorb_row`, then `sweeps` one-site ALS sweeps that maximise
+    <P|Phi> over the candidate MPS P at fixed bond dimensions, Phi = the row
+    applied to `mps`.  The zip-up leaves P in mixed canonical form with the
+    centre at the last column it visited; each sweep runs from that end to
+    the other and back, every column set to its environment in the overlap
+    (fit_site) and re-orthonormalised by a QR (left-isometric, moving right)
+    or an LQ (right-isometric, moving left), the triangular factor dropped
+    (the next column is recomputed from its environment).  The centre's
+    Frobenius norm n is divided out and ln n returned, as absorb_row.
+    ``Trow[c]`` is [l, r, in, out] as in absorb_row."""
+    P, ln0 = absorb_row(mps, Trow, Dc, left_to_right)
+    if ln0 == -math.inf or sweeps == 0:
+        return P, ln0
+    L = len(Trow)
+    # the zip-up divided the norm out of its last tensor; restore it so the
+    # centre carries the scale while sweeping
+    last = L - 1 if left_to_right else 0
+    P[last] = P[last] * math.exp(ln0)
+    Tz = [t.transpose(0, 1, 2, 3) for t in Trow]           # [l, r, in, out]
+
+    def left_env(c):          # F_{c-1}[a, l, a'] of columns < c
+        F = np.ones((1, 1, 1))
+        for k in range(c):
+            F = col1_left(F, mps[k], Tz[k], P[k])
+        return F
+
+    def right_env(c):         # G_{c+1}[b, r, b'] of columns > c
+        G = np.ones((1, 1, 1))
+        for k in reversed(range(c + 1, L)):
+            G = col1_right(G, mps[k], Tz[k], P[k])
+        return G
+
+    order_rl = list(reversed(range(L)))
+    order_lr = list(range(L))
+    passes = []
+    for _ in range(sweeps):
+        passes += [order_rl, order_lr] if left_to_right else [order_lr, order_rl]
+    centre = last
+    for cols in passes:
+        moving_left = cols[0] > cols[-1]
+        for idx, c in enumerate(cols):
+            X = fit_site(left_env(c), mps[c], Tz[c], right_env(c))      # [a', d, b']
+            a, d, b = X.shape
+            last_of_pass = idx == len(cols) - 1
+            if last_of_pass:
+                P[c] = X
+                centre = c
+            elif moving_left:
+                Q, _ = np.linalg.qr(X.reshape(a, d * b).T)           # X^T = Q R -> X = R^T Q^T
+                k = Q.shape[1]
+                Pn = np.zeros((a, d * b))
+                Pn[:k] = Q.T
+                P[c] = Pn.reshape(a, d, b)
+            else:
+                Q, _ = np.linalg.qr(X.reshape(a * d, b))
+                k = Q.shape[1]
+                Pn = np.zeros((a * d, b))
+                Pn[:, :k] = Q
+                P[c] = Pn.reshape(a, d, b)
+    n = float(np.linalg.norm(P[centre]))
+    if n == 0.0:
+        return P, -math.inf
+    P[centre] = P[centre] / n
+    return P, math.log(n)
+
+
 def trivial_mps(L: int):
     return [np.ones((1, 1, 1)) for _ in range(L)]
 
 
-def top_envs(T, Ly: int, Lx: int, Dc: int, perturb=None):
+def _absorb(mps, Trow, Dc, left_to_right, perturb, fit_sweeps):
+    if fit_sweeps:
+        return absorb_row_fit(mps, Trow, Dc, left_to_right, fit_sweeps)
+    return absorb_row(mps, Trow, Dc, left_to_right, perturb=perturb)
+
+
+def top_envs(T, Ly: int, Lx: int, Dc: int, perturb=None, fit_sweeps=0):
     """Upper environments U_r (rows 0..r absorbed), r = -1..Ly-1, as a list indexed r+1.
 
     Row r is absorbed left-to-right when r is even, right-to-left when odd.
@@ -214,7 +298,7 @@ def top_envs(T, Ly: int, Lx: int, Dc: int, perturb=None):
     envs = [(trivial_mps(Lx), 0.0)]
     mps, ls = envs[0]
     for r in range(Ly):
-        mps, ln = absorb_row(mps, rows[r], Dc, left_to_right=(r % 2 == 0), perturb=perturb)
+        mps, ln = _absorb(mps, rows[r], Dc, r % 2 == 0, perturb, fit_sweeps)
         ls += ln
         envs.append((mps, ls))
         if ln == -math.inf:
@@ -224,7 +308,7 @@ def top_envs(T, Ly: int, Lx: int, Dc: int, perturb=None):
     return envs
 
 
-def bottom_envs(T, Ly: int, Lx: int, Dc: int, perturb=None):
+def bottom_envs(T, Ly: int, Lx: int, Dc: int, perturb=None, fit_sweeps=0):
     """Lower environments L_r (rows r..Ly-1 absorbed), r = Ly..0, as a list indexed r.
 
     Built from the bottom: the j-th absorbed row (j = Ly-1-r) goes
@@ -238,7 +322,7 @@ def bottom_envs(T, Ly: int, Lx: int, Dc: int, perturb=None):
     for r in reversed(range(Ly)):
         j = Ly - 1 - r
         flipped = [t.transpose(0, 1, 3, 2) for t in rows[r]]
-        mps, ln = absorb_row(mps, flipped, Dc, left_to_right=(j % 2 == 0), perturb=perturb)
+        mps, ln = _absorb(mps, flipped, Dc, j % 2 == 0, perturb, fit_sweeps)
         ls += ln
         envs[r] = (mps, ls)
         if ln == -math.inf:
@@ -256,10 +340,11 @@ def close_chain(mps) -> float:
     return float(v[0])
 
 
-def amplitude(A, spins, Ly, Lx, Dc):
-    """(ln|psi|, sign psi) from the top-down boundary-MPS sweep (Fig. 1d)."""
+def amplitude(A, spins, Ly, Lx, Dc, fit_sweeps=0):
+    """(ln|psi|, sign psi) from the top-down boundary-MPS sweep (Fig. 1d);
+    fit_sweeps > 0 takes the variational-fit truncation (absorb_row_fit)."""
     T = project(A, spins, Ly, Lx)
-    mps, ls = top_envs(T, Ly, Lx, Dc)[Ly]
+    mps, ls = top_envs(T, Ly, Lx, Dc, fit_sweeps=fit_sweeps)[Ly]
     if ls == -math.inf:
         return -math.inf, 0
     v = close_chain(mps)
@@ -332,13 +417,14 @@ class Evaluation:
 PEPS_OK, PEPS_EINVAL, PEPS_ENUMERIC = 0, 1, 5
 
 
-def evaluate(A, spins, Ly, Lx, Dc, J1, J2, want_O=True, perturb=None):
+def evaluate(A, spins, Ly, Lx, Dc, J1, J2, want_O=True, perturb=None, fit_sweeps=0):
     """ln|psi|, sign, E_loc (Sec. II, E(S)) and Delta = B/W (Sec. II) for one configuration.
 
     Ratios W(S')/W(S) and Delta reuse the environments of S: a pair inside
     row r uses <U_{r-1}| row r |L_{r+1}>, a pair across rows r, r+1 (vertical
     or diagonal) uses <U_{r-1}| rows r, r+1 |L_{r+2}>; each ratio and each
-    Delta is divided by the W of the same sandwich.
+    Delta is divided by the W of the same sandwich.  fit_sweeps > 0 builds
+    the environments with the variational-fit truncation (absorb_row_fit).
     """
     ev = Evaluation()
     N = Ly * Lx
@@ -348,8 +434,8 @@ def evaluate(A, spins, Ly, Lx, Dc, J1, J2, want_O=True, perturb=None):
         return ev
     D = A.shape[2]
     T = project(A, spins, Ly, Lx)
-    up = top_envs(T, Ly, Lx, Dc, perturb)
-    dn = bottom_envs(T, Ly, Lx, Dc, perturb)
+    up = top_envs(T, Ly, Lx, Dc, perturb, fit_sweeps)
+    dn = bottom_envs(T, Ly, Lx, Dc, perturb, fit_sweeps)
     mps, ls = up[Ly]
     v = close_chain(mps) if ls != -math.inf else 0.0
     if v == 0.0:
