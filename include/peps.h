@@ -194,6 +194,20 @@ peps_status peps_mc_sweep(peps_ctx* ctx, uint64_t* S_dev, int n, int nsweeps, ui
 peps_status peps_correlations(peps_ctx* ctx, const uint64_t* S_dev, int n, const int* sites_host, int nc,
                               double* m2_dev, double* corr_dev, int32_t* status_dev);
 
+/* Truncation mode of the boundary MPS (Sec. II, Fig. 1d).  fit_sweeps = 0
+ * (the default): zip-up with SVD truncation to Dc at every column.
+ * fit_sweeps > 0: the variational-fit truncation, the boundary-MPS method by
+ * variational compression: after the zip-up, fit_sweeps one-site ALS sweeps
+ * (each from the zip-up's last column to the other end and back) maximise the
+ * overlap of the new boundary MPS with the uncut row applied to the old one,
+ * at the zip-up's bond dimensions; every column is set to its environment in
+ * that overlap and re-orthonormalised by a QR or LQ (Householder), the
+ * centre ends where the zip-up left it.  Applies to every boundary sweep of
+ * the context (evaluations, gradient, Metropolis, correlations).  Results
+ * differ from the zip-up's (a different truncation) and equal exact
+ * contraction when nothing is cut.  fit_sweeps <= 64. */
+peps_status peps_set_truncation(peps_ctx* ctx, int fit_sweeps);
+
 /* Environment cache.  With on != 0 a context keeps, next to the boundary
  * environments in its workspace, a copy of the configurations they belong
  * to.  A later peps_evaluate, peps_gradient or peps_correlations call whose

@@ -877,6 +877,7 @@ peps_status peps_create(const peps_params* p, const double* A_host, void* stream
   c->g.nwords = (N + 63) / 64;
   c->g.J1 = p->J1;
   c->g.J2 = p->J2;
+  c->g.fit = 0;
   c->stream = (cudaStream_t)stream;
   c->elem = p->prec == PEPS_FP64 ? 8 : 4;
   int dev = 0;
@@ -1071,6 +1072,16 @@ peps_status peps_correlations(peps_ctx* c, const uint64_t* S, int n, const int* 
   if (n == 0) return PEPS_OK;
   if (c->elem == 8) return correlations_impl<double>(c, S, n, sites_host, nc, m2_dev, corr_dev, status_dev);
   return correlations_impl<float>(c, S, n, sites_host, nc, m2_dev, corr_dev, status_dev);
+}
+
+peps_status peps_set_truncation(peps_ctx* c, int fit_sweeps) {
+  if (!c) return fail(PEPS_EINVAL, "null context");
+  if (fit_sweeps < 0 || fit_sweeps > 64) return fail(PEPS_EINVAL, "need 0 <= fit_sweeps <= 64");
+  if (c->parent) return fail(PEPS_EINVAL, "set the truncation on the model's context, not a serving worker");
+  c->g.fit = fit_sweeps;
+  c->cache_dirty = true;   // cached environments belong to the other truncation
+  drop_graphs(c);          // the workspace slots change size
+  return PEPS_OK;
 }
 
 peps_status peps_set_env_cache(peps_ctx* c, int on) {

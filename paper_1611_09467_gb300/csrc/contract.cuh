@@ -130,6 +130,20 @@ PEPS_HD GemmDesc site_env_step(int s, int D, int Dc) {
   }
 }
 
+// Environment of the candidate tensor in the overlap <P| Mu T> (the
+// variational-fit truncation): the single-row left transfer with the Md slot
+// left open.
+//   P[a',d,b'] = sum F[a,l,a'] Mu[a,u,b] T[l,r,u,d] G[b,r,b'].
+//   s0, s1: as col1_left_step (P[a'][b][l][u], then Q[b][r][a'][d])
+//   s2: P[a'][d][b'] = Q . G   (sum b,r)
+PEPS_HD GemmDesc fit_site_step(int s, int D, int Dc) {
+  if (s < 2) return col1_left_step(s, D, Dc);
+  return gemm(Dc * D, Dc, Dc * D,
+              ix1(1), kx(D, D * Dc * D, Dc * D),             // A = Q[b][r][a'][d]: rows (a',d), k = (b,r)
+              kx(D, D * Dc, Dc), ix1(1),                     // B = G[b][r][b']: k = (b,r), cols b'
+              ix1(Dc), ix1(1));                              // C = P[a'][d][b']
+}
+
 // Two-row left transfer (sandwich <U_{r-1}| rows r,r+1 |L_{r+2}>):
 //   E_c[b,r1,r2,b'] = sum E_{c-1}[a,l1,l2,a'] Mu[a,u1,b] T1[l1,r1,u1,m] T2[l2,r2,m,d2] Md[a',d2,b'].
 //   s0: P1[l2][a'][b][l1][u1]  = E . Mu   (sum a)

@@ -251,7 +251,7 @@ __device__ void cta_gemm(const GemmDesc& g, const R* A, const R* B, R* __restric
 }
 
 // ------------------------------------------------- contraction programs
-enum OpId { OP_COL1_LEFT = 0, OP_COL1_RIGHT = 1, OP_SITE_ENV = 2, OP_COL2_LEFT = 3, OP_COL2_RIGHT = 4 };
+enum OpId { OP_COL1_LEFT = 0, OP_COL1_RIGHT = 1, OP_SITE_ENV = 2, OP_COL2_LEFT = 3, OP_COL2_RIGHT = 4, OP_FIT_SITE = 5 };
 enum BufId { IN0 = 0, IN1, IN2, IN3, IN4, TMP0, TMP1, OUT };
 struct Step {
   int s, a, b, c;
@@ -265,8 +265,10 @@ PEPS_HD int op_nsteps(int op) { return (op == OP_COL2_LEFT || op == OP_COL2_RIGH
 //   SITE_ENV  : IN0 = F_{c-1}, IN1 = Mu, IN2 = Md, IN3 = G_{c+1}  -> B_c
 //   COL2_LEFT : IN0 = E_{c-1}, IN1 = Mu, IN2 = T1, IN3 = T2, IN4 = Md -> E_c
 //   COL2_RIGHT: IN0 = H_{c+1}, IN1 = Mu, IN2 = T1, IN3 = T2, IN4 = Md -> H_c
+//   FIT_SITE  : IN0 = F_{c-1}, IN1 = Mu, IN2 = T, IN3 = G_{c+1}   -> P_c
 PEPS_HD Step op_step_bufs(int op, int s) {
   switch (op) {
+    case OP_FIT_SITE:
     case OP_COL1_LEFT:
       return s == 0 ? Step{0, IN0, IN1, TMP0} : s == 1 ? Step{1, TMP0, IN2, TMP1} : Step{2, TMP1, IN3, OUT};
     case OP_COL1_RIGHT:
@@ -291,6 +293,7 @@ PEPS_HD GemmDesc op_desc(int op, int s, int D, int Dc) {
     case OP_COL1_LEFT: return col1_left_step(s, D, Dc);
     case OP_COL1_RIGHT: return col1_right_step(s, D, Dc);
     case OP_SITE_ENV: return site_env_step(s, D, Dc);
+    case OP_FIT_SITE: return fit_site_step(s, D, Dc);
     case OP_COL2_LEFT: return col2_left_step(s, D, Dc);
     default: return col2_right_step(s, D, Dc);
   }

@@ -47,7 +47,7 @@ bool wm_fits_smem(const Geometry& g, size_t elem) {
 
 static size_t zip_elems(const Geometry& g, bool wm_in_smem) {
   const size_t Dc = g.Dc, D = g.D, P = Dc * D;
-  return 2 * Dc * Dc * D + Dc * Dc * D * D + P * P + trunc_ws_elems((int)P, g.Dc, !wm_in_smem);
+  return 2 * Dc * Dc * D + Dc * Dc * D * D + P * P + trunc_ws_elems((int)P, g.Dc, !wm_in_smem) + 64 + fit_elems(g);
 }
 
 size_t boundary_slot_elems(const Geometry& g, bool wm_in_smem) {
@@ -176,14 +176,16 @@ __global__ void __launch_bounds__(kThreads) k_boundary(KArgs<R> a, int dirs) {
   smem_split<R>(smem_raw, g, true, a.smem_wm != 0, gsm, gism);
   carve_zip<R>(g, p, zb, a.smem_wm ? gsm : nullptr, red, dred, wv, gsm, gism);
   for (int i = threadIdx.x; i <= g.Lx; i += blockDim.x) ones[i] = 1;
+  // items direction-major: consecutive items (one per CTA) share a direction,
+  // so sweeps the environment cache skips do not leave half the CTAs idle
   for (int item = blockIdx.x; item < a.n * dirs; item += gridDim.x)
-    boundary_item<R>(a, item / dirs, item % dirs, p, zb, red, sp, ones);
+    boundary_item<R>(a, item % a.n, item / a.n, p, zb, red, sp, ones);
 }
 
 // The boundary sweeps of several models (lattices, D, Dc of one precision) in
 // one persistent launch.  Work items are numbered model after model; start[m]
 // is the first item of model m (start[nm] = total), each model contributing
-// n * dirs items.  Every CTA has one scratch slot of slot_elems reals, sized
+// n * dirs items (direction-major within a model).  Every CTA has one scratch slot of slot_elems reals, sized
 // for the largest model, and dynamic shared memory for the largest model; a
 // CTA lays its slot and shared memory out again whenever its next item
 // belongs to another model.  Per configuration the arithmetic is that of
@@ -217,7 +219,7 @@ __global__ void __launch_bounds__(kThreads) k_boundary_packed(const KArgs<R>* __
       cur = m;
     }
     const int local = item - start[m];
-    boundary_item<R>(a, local / dirs, local % dirs, p, zb, red, sp, ones);
+    boundary_item<R>(a, local % a.n, local / a.n, p, zb, red, sp, ones);
   }
 }
 
@@ -697,6 +699,7 @@ static peps_status amplitudes_static_impl(const peps_params* p, const void* A_de
   g.nwords = (g.N + 63) / 64;
   g.J1 = p->J1;
   g.J2 = p->J2;
+  g.fit = 0;
   const bool wm = wm_fits_smem(g, sizeof(R));
   const size_t slot = static_slot_elems(g, wm);
   const size_t slots = kStaticScratchBytes / (slot * sizeof(R));

@@ -22,6 +22,7 @@ constexpr int kFlagTimeout = 2;      // a bounded device wait gave up
 struct Geometry {
   int Lx, Ly, D, Dc, N, nwords;
   double J1, J2;
+  int fit;               // variational-fit sweeps after each zip-up (0: the zip-up truncation alone)
 };
 
 template <typename R>

@@ -8,7 +8,7 @@
 //   1. M_i = Gamma_i with the weights of its three other bonds and of the
 //      bond itself absorbed, as a matrix [(outer legs), (s, x)]; M_j likewise
 //      (without the bond's weight).  Column-major in the CTA's scratch slot.
-//   2. Householder QR of each (m = D^3 rows, n = 2D columns): M = Q R.
+//   2. Householder QR of each (m = D^3 rows, n = 2D columns): M = Q R (qr.cuh).
 //   3. Theta[(a, s_i'), (s_j', b)] = sum G[s_i' s_j', s_i s_j] R_i[a, (s_i, x)] R_j[b, (s_j, x)].
 //   4. One-sided Jacobi SVD of Theta (columns rotated until orthogonal):
 //      the D largest singular values, normalised, are the new weight; the
@@ -30,6 +30,7 @@
 
 #include "../../include/peps.h"
 #include "kernels.h"
+#include "qr.cuh"
 
 namespace peps {
 namespace su {
@@ -94,76 +95,6 @@ __device__ double gate_entry(int kind, double J1, double J2, double dtau, int p,
   const double ps = (p == 1 ? 1.0 : (p == 2 ? -1.0 : 0.0)) * (q == 1 ? 1.0 : (q == 2 ? -1.0 : 0.0)) * 0.5;
   const double id = p == q ? 1.0 : 0.0;
   return exp(-dtau * J * 0.25) * (id - ps) + exp(0.75 * dtau * J) * ps;
-}
-
-// Householder QR in place of the column-major m x n matrix M: R in the upper
-// triangle of the first k = min(m, n) rows, reflector k as v_k = 1 (implicit)
-// and M[k+1.., k] below the diagonal, H_k = I - tau_k v v^T.
-__device__ void house_qr(double* M, int m, int n, double* tau, double* red) {
-  const int k_end = min(m, n);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  __shared__ double s_beta, s_scale;
-  for (int k = 0; k < k_end; ++k) {
-    double* x = M + (size_t)k * m;
-    double s2 = 0.0;
-    for (int r = k + 1 + threadIdx.x; r < m; r += blockDim.x) s2 += x[r] * x[r];
-    s2 = block_sum_d(s2, red);
-    if (threadIdx.x == 0) {
-      const double alpha = x[k];
-      if (s2 == 0.0) {
-        tau[k] = 0.0;
-        s_scale = 0.0;
-      } else {
-        const double nrm = sqrt(alpha * alpha + s2);
-        const double beta = alpha <= 0.0 ? nrm : -nrm;
-        tau[k] = (beta - alpha) / beta;
-        s_scale = 1.0 / (alpha - beta);
-        x[k] = beta;
-      }
-    }
-    __syncthreads();
-    const double sc = s_scale;
-    if (sc != 0.0)
-      for (int r = k + 1 + threadIdx.x; r < m; r += blockDim.x) x[r] *= sc;
-    __syncthreads();
-    const double t = tau[k];
-    if (t != 0.0) {
-      for (int c = k + 1 + warp; c < n; c += kW) {
-        double* y = M + (size_t)c * m;
-        double w = 0.0;
-        for (int r = k + 1 + lane; r < m; r += 32) w += x[r] * y[r];
-        w = warp_sum(w) + y[k];
-        w *= t;
-        if (lane == 0) y[k] -= w;
-        for (int r = k + 1 + lane; r < m; r += 32) y[r] -= w * x[r];
-      }
-    }
-    __syncthreads();
-  }
-  (void)s_beta;
-}
-
-// N <- H_0 H_1 ... H_{k-1} N for the reflectors stored in M (house_qr), N
-// column-major m x n.
-__device__ void apply_q(const double* M, const double* tau, double* N, int m, int n) {
-  const int k_end = min(m, n);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int k = k_end - 1; k >= 0; --k) {
-    const double t = tau[k];
-    if (t != 0.0) {
-      const double* v = M + (size_t)k * m;
-      for (int c = warp; c < n; c += kW) {
-        double* y = N + (size_t)c * m;
-        double w = 0.0;
-        for (int r = k + 1 + lane; r < m; r += 32) w += v[r] * y[r];
-        w = warp_sum(w) + y[k];
-        w *= t;
-        if (lane == 0) y[k] -= w;
-        for (int r = k + 1 + lane; r < m; r += 32) y[r] -= w * v[r];
-      }
-    }
-    __syncthreads();
-  }
 }
 
 // One-sided Jacobi SVD of the row-major m2 x n2 matrix T (shared memory):
@@ -296,8 +227,8 @@ __global__ void __launch_bounds__(kT) k_su_bond(Args a) {
   }
   __syncthreads();
   // ---- 2. QR of both
-  house_qr(Mi, m, n, tau_i, red);
-  house_qr(Mj, m, n, tau_j, red);
+  qr::house_qr<double>(Mi, m, n, tau_i, red);
+  qr::house_qr<double>(Mj, m, n, tau_j, red);
   const int ki = min(m, n), kj = min(m, n);
   const int m2 = 2 * ki, n2 = 2 * kj;
   // ---- 3. Theta[(a, s_i'), (s_j', b)]
@@ -364,8 +295,8 @@ __global__ void __launch_bounds__(kT) k_su_bond(Args a) {
     Nj[e] = vj;
   }
   __syncthreads();
-  apply_q(Mi, tau_i, Ni, m, n);
-  apply_q(Mj, tau_j, Nj, m, n);
+  qr::apply_q<double>(Mi, tau_i, Ni, m, n, n);
+  qr::apply_q<double>(Mj, tau_j, Nj, m, n, n);
   // ---- back to Gamma with the outer weights divided out (the bond weight
   // was just written; no thread reads it below)
   for (int e = threadIdx.x; e < 2 * D4; e += blockDim.x) {

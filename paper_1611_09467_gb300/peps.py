@@ -62,6 +62,7 @@ def lib():
         "peps_set_graphs": [P, i],
         "peps_measure_peaks": [P],
         "peps_set_env_cache": [P, i],
+        "peps_set_truncation": [P, i],
         "peps_correlations": [P, P, i, P, i, P, P, P],
         "peps_su_create": [ctypes.POINTER(Params), P, ctypes.POINTER(P)],
         "peps_su_destroy": [P],
@@ -103,7 +104,8 @@ def exported_symbols():
              "peps_status_str", "peps_last_error", "peps_debug_host_op", "peps_debug_host_zip",
              "peps_profile_enable", "peps_profile_read", "peps_amplitudes_static", "peps_go_step",
              "peps_gradient_sums", "peps_gradient_sums_len", "peps_gradient_finalize", "peps_set_graphs",
-             "peps_graph_stats", "peps_correlations", "peps_set_env_cache", "peps_measure_peaks", "peps_server_create",
+             "peps_graph_stats", "peps_correlations", "peps_set_env_cache", "peps_set_truncation", "peps_measure_peaks",
+             "peps_server_create",
              "peps_server_destroy", "peps_server_submit", "peps_server_submit_chain", "peps_server_set_packing",
              "peps_server_poll", "peps_server_stats", "peps_su_create", "peps_su_destroy", "peps_su_evolve", "peps_su_to_peps",
              "peps_autotune", "peps_tuned_config", "peps_packer_create", "peps_packer_destroy",
@@ -330,6 +332,10 @@ class PEPS:
         st = torch.empty(n, dtype=torch.int32, device=S.device)
         check(lib().peps_correlations(self.h, _ptr(S), n, _ptr(sites), len(sites), _ptr(m2), _ptr(C), _ptr(st)))
         return dict(m2=m2, corr=C, status=st)
+
+    def set_truncation(self, fit_sweeps=0):
+        """0: zip-up SVD truncation; > 0: that many variational-fit sweeps after it."""
+        check(lib().peps_set_truncation(self.h, int(fit_sweeps)))
 
     def set_env_cache(self, on=True):
         """Keep boundary environments across calls for unchanged configurations."""
