@@ -156,7 +156,7 @@ __device__ void fit_orthonormalise(R* X, int a, int o, int b, int D, int Dc, boo
 // value is the exponent the centre tensor is scaled by.  bdo: the tensors'
 // bond dimensions.
 template <typename R>
-__device__ int fit_row(const KArgs<R>& a, const R* Min, R* Mout, int row, int dir, bool lr, const uint64_t* sp,
+__device__ __noinline__ int fit_row(const KArgs<R>& a, const R* Min, R* Mout, int row, int dir, bool lr, const uint64_t* sp,
                        const int* bdo, ZipBufs<R>& zb, R* red) {
   const Geometry& g = a.g;
   const int D = g.D, Dc = g.Dc, Lx = g.Lx;

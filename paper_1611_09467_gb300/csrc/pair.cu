@@ -9,7 +9,7 @@ namespace peps {
 // ---------------------------------------------------------------- k_pair
 template <typename R>
 __global__ void __launch_bounds__(kThreads) k_pair(KArgs<R> a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ R red[64];
   __shared__ uint64_t sp[kMaxWords];
   const Geometry& g = a.g;
@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(kThreads) k_pair(KArgs<R> a) {
 // fixed (D, Dc).  Transfers are stored [x'][x][y1][y2] (see pair_fused.cuh).
 template <typename R, int D, int Dc>
 __global__ void __launch_bounds__(kThreads) k_pair_fused(KArgs<R> a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ R red[64];
   __shared__ uint64_t sp[kMaxWords];
   R* sm = reinterpret_cast<R*>(smem_raw);
