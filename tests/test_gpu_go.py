@@ -125,3 +125,42 @@ def test_go_loop_on_the_device_descends_and_respects_ed():
     assert e1 > e_ed
     assert np.mean(sampled[-5:]) < np.mean(sampled[:5]) - 0.1
     p.close()
+
+
+def test_simple_update_then_go_on_the_device():
+    """The paper's optimisation pipeline (Sec. III) on the device, 4x4, J2 = 0,
+    D = 2: the simple update from the seeded random tensors to convergence
+    (dtau = 0.01, then 0.001, each until the relative change is below 1e-6;
+    peps_su_*), its PEPS as the start of the GO loop (Metropolis with 1024
+    chains -> peps_gradient -> peps_go_step, 60 steps of the paper's dt
+    schedule).  The exact energy of the SU state equals the oracle's SU
+    energy (-0.55355), the GO steps lower it by more than 0.005 per site, and
+    it stays above ED (Table I: SU -0.54557 and GO -0.570872 at D = 2)."""
+    from paper_1611_09467_gb300.peps import PEPS, SimpleUpdate
+    from oracle import simple_update as SU
+    L, D, Dc = 4, 2, 4
+    N = L * L
+    Gam, lam = SU.init_state(L, L, D, 301)
+    h, v = O.nn_bonds(L, L)
+    su = SimpleUpdate(Gam, np.stack([lam[b] for b in h + v]), L, L, D, J1=1.0, J2=0.0)
+    for dtau in (0.01, 0.001):
+        for _ in range(200):
+            if su.evolve(dtau, 50) < 1e-6:
+                break
+    A0 = su.to_peps().cpu().numpy().reshape(N, 2, D, D, D, D)
+    su.close()
+    e_su = _exact_energy_per_site(A0, L, 0.0)
+    e_ed = O.ground_energy(L, L, 1.0, 0.0) / N
+    p = PEPS(A0, L, L, D, Dc, J1=1.0, J2=0.0, prec="fp64")
+    S = torch.from_numpy(inputs.pack_spins(inputs.random_sz0(1024, N, 305)).view(np.int64)).cuda()
+    p.mc_sweep(S, nsweeps=5, seed=306, chain0=0, sweep0=0)
+    for step in range(60):
+        p.mc_sweep(S, nsweeps=2, seed=306, chain0=0, sweep0=5 + 2 * step)
+        g = p.gradient(S)
+        p.go_step(g["grad"], O.go_dt(step), seed=307, step=step, copy_back=(step == 59))
+    e_go = _exact_energy_per_site(p.A, L, 0.0)
+    print("exact energy per site: SU %.6f, after 60 GO steps %.6f, ED %.6f" % (e_su, e_go, e_ed))
+    assert abs(e_su - (-0.5535529)) < 1e-5
+    assert e_go < e_su - 0.005
+    assert e_go > e_ed
+    p.close()
