@@ -250,6 +250,171 @@ __device__ void cta_gemm(const GemmDesc& g, const R* A, const R* B, R* __restric
   else gemm_tiles<R, 512, 16, 8, 4>(g, A, B, C, accumulate, sm, ism);
 }
 
+// C = A B for a descriptor with K <= KM, the whole reduction staged at once:
+// per tile of TM rows every load is issued before the first store to shared
+// memory, so one load latency is exposed per tile rather than one per 16-wide
+// K chunk, and a tile costs two barriers.  FP32 tiles are multiplied with
+// packed FP32x2 multiply-adds.  Each output is the same left-to-right chain
+// of fused multiply-adds over k as in gemm_tiles, so the results are
+// identical.  `sm` holds K * (TM + TN) reals; `ism` the offset tables.
+template <typename R, int TM, int TN, int MT, int NT, int KM>
+__device__ __noinline__ void gemm_wk(const GemmDesc& g, const R* A, const R* B, R* __restrict__ C, R* sm,
+                                     int* ism) {
+  constexpr int GX = TN / NT, GY = TM / MT;
+  static_assert(GX * GY == kThreads, "thread grid must cover the CTA");
+  static_assert(MT % 4 == 0 && NT % 4 == 0, "tiles are read as 16-byte groups");
+  constexpr int LA = TM * KM / kThreads, LB = TN * KM / kThreads;
+  const int K = g.K;
+  R* As = sm;            // [K][TM]
+  R* Bs = sm + K * TM;   // [K][TN]
+  int* ktA = ism;
+  int* ktB = ism + KM;
+  int* rA = ism + 2 * KM;
+  int* rC = rA + TM;
+  int* cB = rC + TM;
+  int* cC = cB + TN;
+  const int tid = threadIdx.x;
+  const int tx = tid % GX, ty = tid / GX;
+  __syncthreads();
+  for (int k = tid; k < K; k += kThreads) {
+    const int k1 = k / g.ak.n2, k2 = k - k1 * g.ak.n2;
+    ktA[k] = k1 * g.ak.s1 + k2 * g.ak.s2;
+    ktB[k] = k1 * g.bk.s1 + k2 * g.bk.s2;
+  }
+  const int tiles_m = (g.M + TM - 1) / TM, tiles_n = (g.N + TN - 1) / TN;
+  for (int bt = 0; bt < g.nb; ++bt) {
+    const R* Ab = A + (size_t)bt * g.sa;
+    const R* Bb = B + (size_t)bt * g.sb;
+    R* Cb = C + (size_t)bt * g.sc;
+    for (int tni = 0; tni < tiles_n; ++tni)
+      for (int tmi = 0; tmi < tiles_m; ++tmi) {
+        const int i0 = tmi * TM, j0 = tni * TN;
+        __syncthreads();
+        for (int e = tid; e < TM; e += kThreads) {
+          const int i = min(i0 + e, g.M - 1);
+          rA[e] = ixoff(g.am, i);
+          rC[e] = ixoff(g.cm, i);
+        }
+        for (int e = tid; e < TN; e += kThreads) {
+          const int j = min(j0 + e, g.N - 1);
+          cB[e] = ixoff(g.bn, j);
+          cC[e] = ixoff(g.cn, j);
+        }
+        __syncthreads();
+        R va[LA], vb[LB];
+#pragma unroll
+        for (int q = 0; q < LA; ++q) {
+          const int e = tid + q * kThreads, kk = e / TM, i = e % TM;
+          va[q] = kk < K ? Ab[rA[i] + ktA[kk]] : R(0);
+        }
+#pragma unroll
+        for (int q = 0; q < LB; ++q) {
+          const int e = tid + q * kThreads, kk = e / TN, j = e % TN;
+          vb[q] = kk < K ? Bb[ktB[kk] + cB[j]] : R(0);
+        }
+#pragma unroll
+        for (int q = 0; q < LA; ++q) {
+          const int e = tid + q * kThreads;
+          if (e / TM < K) As[e] = va[q];
+        }
+#pragma unroll
+        for (int q = 0; q < LB; ++q) {
+          const int e = tid + q * kThreads;
+          if (e / TN < K) Bs[e] = vb[q];
+        }
+        __syncthreads();
+        R acc[MT][NT];
+        if constexpr (sizeof(R) == 4) {
+          float2 acc2[MT][NT / 2];
+#pragma unroll
+          for (int m = 0; m < MT; ++m)
+#pragma unroll
+            for (int n = 0; n < NT / 2; ++n) acc2[m][n] = make_float2(0.f, 0.f);
+#pragma unroll 4
+          for (int kk = 0; kk < K; ++kk) {
+            float a[MT], b[NT];
+#pragma unroll
+            for (int m = 0; m < MT; m += 4) {
+              const float4 t = *reinterpret_cast<const float4*>(As + kk * TM + ty * MT + m);
+              a[m] = t.x; a[m + 1] = t.y; a[m + 2] = t.z; a[m + 3] = t.w;
+            }
+#pragma unroll
+            for (int n = 0; n < NT; n += 4) {
+              const float4 t = *reinterpret_cast<const float4*>(Bs + kk * TN + tx * NT + n);
+              b[n] = t.x; b[n + 1] = t.y; b[n + 2] = t.z; b[n + 3] = t.w;
+            }
+#pragma unroll
+            for (int m = 0; m < MT; ++m)
+#pragma unroll
+              for (int n = 0; n < NT / 2; ++n)
+                acc2[m][n] = __ffma2_rn(make_float2(a[m], a[m]), make_float2(b[2 * n], b[2 * n + 1]), acc2[m][n]);
+          }
+#pragma unroll
+          for (int m = 0; m < MT; ++m)
+#pragma unroll
+            for (int n = 0; n < NT / 2; ++n) {
+              acc[m][2 * n] = acc2[m][n].x;
+              acc[m][2 * n + 1] = acc2[m][n].y;
+            }
+        } else {
+#pragma unroll
+          for (int m = 0; m < MT; ++m)
+#pragma unroll
+            for (int n = 0; n < NT; ++n) acc[m][n] = R(0);
+          for (int kk = 0; kk < K; ++kk) {
+            R a[MT], b[NT];
+#pragma unroll
+            for (int m = 0; m < MT; ++m) a[m] = As[kk * TM + ty * MT + m];
+#pragma unroll
+            for (int n = 0; n < NT; ++n) b[n] = Bs[kk * TN + tx * NT + n];
+#pragma unroll
+            for (int m = 0; m < MT; ++m)
+#pragma unroll
+              for (int n = 0; n < NT; ++n) acc[m][n] = fma(a[m], b[n], acc[m][n]);
+          }
+        }
+        int cc[NT];
+#pragma unroll
+        for (int n = 0; n < NT; ++n) cc[n] = cC[tx * NT + n];
+#pragma unroll
+        for (int m = 0; m < MT; ++m) {
+          const int i = ty * MT + m;
+          if (i0 + i >= g.M) break;
+          const int rc = rC[i];
+#pragma unroll
+          for (int n = 0; n < NT; ++n) {
+            if (j0 + tx * NT + n >= g.N) break;
+            Cb[rc + cc[n]] = acc[m][n];
+          }
+        }
+      }
+  }
+  __syncthreads();
+}
+
+// Reals of shared scratch gemm_wk needs for a descriptor, or 0 when the
+// descriptor is outside its shapes (cta_gemm takes those).
+PEPS_HD int zip_gemm_reals(const GemmDesc& g) {
+  if (g.N > 64 && g.N <= 128 && g.K <= 16) return g.K * (64 + 128);
+  if (g.N <= 64 && g.K <= 64) return g.K * (128 + 64);
+  return 0;
+}
+
+// C = A B for the zip-up contractions: gemm_wk when the descriptor fits it
+// and `sm_reals` reals of shared scratch, else cta_gemm.  Same results either
+// way.
+template <typename R>
+__device__ __noinline__ void zip_gemm(const GemmDesc& g, const R* A, const R* B, R* __restrict__ C, R* sm, int* ism,
+                         int sm_reals) {
+  const int need = zip_gemm_reals(g);
+  if (need > 0 && need <= sm_reals) {
+    if (g.N > 64) gemm_wk<R, 64, 128, 4, 8, 16>(g, A, B, C, sm, ism);
+    else gemm_wk<R, 128, 64, 8, 4, 64>(g, A, B, C, sm, ism);
+  } else {
+    cta_gemm<R>(g, A, B, C, false, sm, ism);
+  }
+}
+
 // ------------------------------------------------- contraction programs
 enum OpId { OP_COL1_LEFT = 0, OP_COL1_RIGHT = 1, OP_SITE_ENV = 2, OP_COL2_LEFT = 3, OP_COL2_RIGHT = 4, OP_FIT_SITE = 5 };
 enum BufId { IN0 = 0, IN1, IN2, IN3, IN4, TMP0, TMP1, OUT };
@@ -342,6 +507,7 @@ struct TruncWork {
   R* gsm;     // GEMM shared scratch (may alias Wm: used only after the reflectors are dead)
   int* gism;
   int Qmax;
+  int wm_shared;   // Wm is in shared memory
 };
 
 // Element counts of the truncation workspace for P, Q <= pq and K <= kmax.
@@ -1113,6 +1279,38 @@ __device__ void cta_topk_left(const R* X, int m, int n, int K, TruncWork<R>& w, 
     __shared__ R bt_g[NBMAX][NBMAX], bt_t[NBMAX][NBMAX], bt_w1[NBMAX][KMAX + NBMAX], bt_w2[NBMAX][KMAX];
     const R* taus = tall ? tauL : tauR;
     const R* scs = tall ? w.tau + 2 * w.Qmax : w.tau + 3 * w.Qmax;
+    if constexpr (sizeof(R) == 4) {
+      // Register-tiled path: the reflectors, their factors and scales move
+      // from global memory to shared memory once (the truncation matrix
+      // buffer is free after the inverse iteration), all loads of a round in
+      // flight together, instead of one exposed load latency per block below.
+      __shared__ float bt_tau[128], bt_scs[128];
+      if (tiled && w.wm_shared && Q <= 128) {
+        R* Ws = w.Wm;
+        const int tot = P * ld;
+        for (int e0 = 0; e0 < tot; e0 += 8 * kThreads) {
+          R v[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const int e = e0 + u * kThreads + tid;
+            v[u] = e < tot ? W[e] : R(0);
+          }
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const int e = e0 + u * kThreads + tid;
+            if (e < tot) Ws[e] = v[u];
+          }
+        }
+        for (int e = tid; e < Q; e += kThreads) {
+          bt_tau[e] = taus[e];
+          bt_scs[e] = scs[e];
+        }
+        W = Ws;
+        taus = bt_tau;
+        scs = bt_scs;
+        __syncthreads();
+      }
+    }
     const int nref = tall ? Q : Q - 1;
     const int NB = K < NBMAX ? K : NBMAX;
     R* Vs = Ub;   // [rowsU][nb]
@@ -1201,19 +1399,47 @@ __device__ void cta_topk_left(const R* X, int m, int n, int K, TruncWork<R>& w, 
       Mns[e] = -0.5f * (a == b ? __fadd_rn(__fsub_rn(s, 1.f), c) : __fadd_rn(s, c));
     }
     __syncthreads();
-    for (int e = tid; e < m * K; e += blockDim.x) {
-      const int i = e / K, k = e % K;
-      float corr = 0.f;
-      for (int a = 0; a < K; ++a) corr = fmaf(Uf[i * K + a], Mns[a * K + k], corr);
-      const float v = Uf[i * K + k] + corr;
-      Uout[ixoff(uo_r, i) + ixoff(uo_c, k)] = v;
-      w.Uk[e] = v;
+    // Up to kNsPer entries per thread, the new U replaces the old one in
+    // shared memory once every thread has read the old one; larger U go to
+    // the global copy.
+    constexpr int kNsPer = 8;
+    const bool u_shared = m * K <= kNsPer * kThreads;
+    float* Us = reinterpret_cast<float*>(Uk);
+    if (u_shared) {
+      float nv[kNsPer];
+#pragma unroll
+      for (int q = 0; q < kNsPer; ++q) {
+        const int e = tid + q * kThreads;
+        if (e < m * K) {
+          const int i = e / K, k = e % K;
+          float corr = 0.f;
+          for (int a = 0; a < K; ++a) corr = fmaf(Uf[i * K + a], Mns[a * K + k], corr);
+          nv[q] = Uf[i * K + k] + corr;
+          Uout[ixoff(uo_r, i) + ixoff(uo_c, k)] = nv[q];
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int q = 0; q < kNsPer; ++q) {
+        const int e = tid + q * kThreads;
+        if (e < m * K) Us[e] = nv[q];
+      }
+    } else {
+      for (int e = tid; e < m * K; e += blockDim.x) {
+        const int i = e / K, k = e % K;
+        float corr = 0.f;
+        for (int a = 0; a < K; ++a) corr = fmaf(Uf[i * K + a], Mns[a * K + k], corr);
+        const float v = Uf[i * K + k] + corr;
+        Uout[ixoff(uo_r, i) + ixoff(uo_c, k)] = v;
+        w.Uk[e] = v;
+      }
     }
     __syncthreads();
     // C' = U_K^T X, X row-major m x n.  One work item is a column j and a
-    // chunk of 8 rows of C'; its X column is read once (coalesced over j).
-    constexpr int CH = 8;
-    const float* Uo = reinterpret_cast<const float*>(w.Uk);
+    // chunk of 8 rows of C'; its X column is read once (coalesced over j),
+    // eight rows at a time so that eight loads are in flight together.
+    constexpr int CH = 8, XB = 8;
+    const float* Uo = u_shared ? Us : reinterpret_cast<const float*>(w.Uk);
     const float* Xf = reinterpret_cast<const float*>(X);
     const int nchunk = (K + CH - 1) / CH;
     for (int item = tid; item < n * nchunk; item += blockDim.x) {
@@ -1221,11 +1447,19 @@ __device__ void cta_topk_left(const R* X, int m, int n, int K, TruncWork<R>& w, 
       float s[CH], c[CH];
 #pragma unroll
       for (int q = 0; q < CH; ++q) s[q] = c[q] = 0.f;
-      for (int i = 0; i < m; ++i) {
-        const float x = Xf[i * n + j];
+      for (int ib = 0; ib < m; ib += XB) {
+        float xb[XB];
 #pragma unroll
-        for (int q = 0; q < CH; ++q)
-          if (a0 + q < K) dot2_step(Uo[i * K + a0 + q], x, s[q], c[q]);
+        for (int u = 0; u < XB; ++u) xb[u] = ib + u < m ? Xf[(ib + u) * n + j] : 0.f;
+#pragma unroll
+        for (int u = 0; u < XB; ++u) {
+          const int i = ib + u;
+          if (i < m) {
+#pragma unroll
+            for (int q = 0; q < CH; ++q)
+              if (a0 + q < K) dot2_step(Uo[i * K + a0 + q], xb[u], s[q], c[q]);
+          }
+        }
       }
 #pragma unroll
       for (int q = 0; q < CH; ++q)

@@ -115,6 +115,7 @@ struct ZipBufs {
   double* dred;   // >= kWarps doubles of shared memory
   R* gsm;         // GEMM shared scratch
   int* gism;
+  int gsm_reals;  // its size in reals (free between truncations)
   TruncWork<R> tw;
   FitBufs<R> fb;
 };
@@ -275,8 +276,9 @@ __device__ double absorb_row(const KArgs<R>& a, const R* Min, R* Mout, int row, 
       z.l = td.l; z.r = td.r;
       z.o = dir == 0 ? td.d : td.u;
       const R* T = tptr(a, row * Lx + c, spin_of(sp, row * Lx + c));
-      cta_gemm<R>(zip_lr_step(0, z, D, Dc, sl, sr, si, so), Cc, Min + (size_t)c * envT, zb.Y, false, zb.gsm, zb.gism);
-      cta_gemm<R>(zip_lr_step(1, z, D, Dc, sl, sr, si, so), zb.Y, T, zb.X, false, zb.gsm, zb.gism);
+      zip_gemm<R>(zip_lr_step(0, z, D, Dc, sl, sr, si, so), Cc, Min + (size_t)c * envT, zb.Y, zb.gsm, zb.gism,
+                  zb.gsm_reals);
+      zip_gemm<R>(zip_lr_step(1, z, D, Dc, sl, sr, si, so), zb.Y, T, zb.X, zb.gsm, zb.gism, zb.gsm_reals);
       const int m = z.k * z.o, n = z.b * z.r;
       if (c < Lx - 1) {
         const int K = min(Dc, min(m, n));
@@ -303,8 +305,9 @@ __device__ double absorb_row(const KArgs<R>& a, const R* Min, R* Mout, int row, 
       z.l = td.l; z.r = td.r;
       z.o = dir == 0 ? td.d : td.u;
       const R* T = tptr(a, row * Lx + c, spin_of(sp, row * Lx + c));
-      cta_gemm<R>(zip_rl_step(0, z, D, Dc, sl, sr, si, so), Min + (size_t)c * envT, Cc, zb.Y, false, zb.gsm, zb.gism);
-      cta_gemm<R>(zip_rl_step(1, z, D, Dc, sl, sr, si, so), zb.Y, T, zb.X, false, zb.gsm, zb.gism);
+      zip_gemm<R>(zip_rl_step(0, z, D, Dc, sl, sr, si, so), Min + (size_t)c * envT, Cc, zb.Y, zb.gsm, zb.gism,
+                  zb.gsm_reals);
+      zip_gemm<R>(zip_rl_step(1, z, D, Dc, sl, sr, si, so), zb.Y, T, zb.X, zb.gsm, zb.gism, zb.gsm_reals);
       const int m = z.o * z.k, n = z.a * z.l;
       if (c > 0) {
         const int K = min(Dc, min(m, n));
@@ -350,6 +353,7 @@ __device__ void carve_zip(const Geometry& g, R*& p, ZipBufs<R>& zb, R* wm_smem, 
   zb.dred = dred;
   zb.gsm = gsm;
   zb.gism = gism;
+  zb.gsm_reals = (int)(reals_region_bytes(g, sizeof(R), true, wm_smem != nullptr) / sizeof(R));
   zb.tw.wv = wv;
   zb.tw.gsm = gsm;
   zb.tw.gism = gism;
@@ -371,6 +375,7 @@ __device__ void carve_zip(const Geometry& g, R*& p, ZipBufs<R>& zb, R* wm_smem, 
   w.Ubs = sh; sh += P * Dc;
   w.Uks = sh;
   w.Qmax = (int)P;
+  w.wm_shared = wm_smem != nullptr;
   w.tau = p; p += 4 * P;
   w.t = p; p += 2 * P;
   w.t2 = p; p += 2 * P;

@@ -15,8 +15,13 @@
 //
 // Shared-memory operand layout (no swizzle): core matrices of 8 rows x 16
 // bytes; element (row, k) of an R x K tile at
-//   (row / 8) * (K / 4) * 32 + (k / 4) * 32 + (row % 8) * 4 + (k % 4)   floats,
-// i.e. leading (K-direction) byte offset 128, stride (8-row) byte offset K*32.
+//   (row / 8) * sbo + (k / 4) * 32 + (row % 8) * 4 + (k % 4)   floats,
+// i.e. leading (K-direction) byte offset 128 and stride (8-row) byte offset
+// 4 sbo.  The B operands and the A operands of s1 and s2 are dense
+// (sbo = K * 8).  The A operands of s3 and s4 are written by lanes that hold
+// the same row of different 8-row groups; their 8-row groups are padded by 16
+// bytes (sbo = K * 8 + 4) so that eight such 16-byte stores fall in distinct
+// banks.
 #pragma once
 
 #include <cstdint>
@@ -37,9 +42,14 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)_
 __device__ __forceinline__ int kmaj(int row, int k, int K) {
   return (row >> 3) * (K >> 2) * 32 + (k >> 2) * 32 + (row & 7) * 4 + (k & 3);
 }
+// The same with an explicit 8-row stride of `sbo` floats.
+__device__ __forceinline__ int kmaj_sbo(int row, int k, int sbo) {
+  return (row >> 3) * sbo + (k >> 2) * 32 + (row & 7) * 4 + (k & 3);
+}
 
-__device__ __forceinline__ uint64_t sdesc(uint32_t addr, int K) {
-  const uint32_t lbo = 128, sbo = (uint32_t)K * 32;
+// Shared-memory matrix descriptor; sbo_bytes = 0 means the dense K * 32.
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, int K, uint32_t sbo_bytes = 0) {
+  const uint32_t lbo = 128, sbo = sbo_bytes ? sbo_bytes : (uint32_t)K * 32;
   return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
          ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
 }
@@ -54,13 +64,14 @@ __device__ __forceinline__ float to_tf32(float x) {
   return __uint_as_float(r);
 }
 
-// One MMA chain D[M x N] (+)= A[M x K] B[N x K]^T, K in steps of 8; single thread.
+// One MMA chain D[M x N] (+)= A[M x K] B[N x K]^T, K in steps of 8; single
+// thread.  a_sbo: A's 8-row stride in bytes (0: dense).
 __device__ __forceinline__ void mma_chain(uint32_t tmem_d, const float* A, const float* B, int M, int N, int K,
-                                          bool accumulate) {
+                                          bool accumulate, uint32_t a_sbo = 0) {
   const uint32_t idesc = idesc_tf32(M, N);
   const uint32_t a0 = smem_u32(A), b0 = smem_u32(B);
   for (int ks = 0; ks < K / 8; ++ks) {
-    const uint64_t ad = sdesc(a0 + ks * 256, K), bd = sdesc(b0 + ks * 256, K);
+    const uint64_t ad = sdesc(a0 + ks * 256, K, a_sbo), bd = sdesc(b0 + ks * 256, K);
     const uint32_t acc = (accumulate || ks > 0) ? 1u : 0u;
     asm volatile(
         "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
@@ -106,7 +117,9 @@ __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::
 }  // namespace tc
 
 struct PairTcSmem {
-  static constexpr int A1 = 128 * 16, B1 = 64 * 16, AB = 8192, B2 = 64 * 64, B3 = 64 * 64, B4 = 16 * 8;
+  // 8-row strides (floats) of the padded A operands of s3 (K = 64) and s4 (K = 8)
+  static constexpr int sbo3 = 64 * 8 + 4, sbo4 = 8 * 8 + 4, tile4 = 16 * sbo4;
+  static constexpr int A1 = 128 * 16, B1 = 64 * 16, AB = 8 * tile4, B2 = 64 * 64, B3 = 64 * 64, B4 = 16 * 8;
   static constexpr int total = A1 + B1 + AB + B2 + B3 + B4;   // floats
 };
 
@@ -216,8 +229,10 @@ static __device__ float pair_step_tc(PairTc& st, bool right, const float* Ein, f
   }
   // Slice s+1 of Ein and Md is loaded into registers as soon as slice s is
   // staged, so the loads complete under slice s's four MMA stages.
-  const int bn = tid >> 2, bxq = (tid & 3) * 4;     // this thread's B1 entries
-  const int mxo = tid >> 1, mdq = (tid & 1) * 4;    // its B4 entries (tid < 32)
+  // this thread's B1 entries (consecutive lanes take consecutive rows, so the
+  // 16-byte stores of a warp fall in distinct banks) and B4 entries (tid < 32)
+  const int bn = tid & 63, bxq = (tid >> 6) * 4;
+  const int mxo = tid & 15, mdq = (tid >> 4) * 4;
   auto load_slice = [&](int s, float (&e)[4], float (&md)[4]) {
     const float* src = Ein + s * (Dc * 64) + bn;
 #pragma unroll
@@ -271,9 +286,10 @@ static __device__ float pair_step_tc(PairTc& st, bool right, const float* Ein, f
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         const int y1o = half * 4 + j;
-        float* dst = AB + tc::kmaj(xo * D + y1o, y2 * D, 64);
-        st4(dst, v[j * 8 + 0], v[j * 8 + 1], v[j * 8 + 2], v[j * 8 + 3]);
-        st4(AB + tc::kmaj(xo * D + y1o, y2 * D + 4, 64), v[j * 8 + 4], v[j * 8 + 5], v[j * 8 + 6], v[j * 8 + 7]);
+        st4(AB + tc::kmaj_sbo(xo * D + y1o, y2 * D, S::sbo3), v[j * 8 + 0], v[j * 8 + 1], v[j * 8 + 2],
+            v[j * 8 + 3]);
+        st4(AB + tc::kmaj_sbo(xo * D + y1o, y2 * D + 4, S::sbo3), v[j * 8 + 4], v[j * 8 + 5], v[j * 8 + 6],
+            v[j * 8 + 7]);
       }
     }
     tc::fence_async_smem();
@@ -281,7 +297,7 @@ static __device__ float pair_step_tc(PairTc& st, bool right, const float* Ein, f
     __syncthreads();
     tc::tc_fence_after();
     // ---- s3: D3[(xo,y1o)][(y2o,d2)]
-    if (tid == 0) tc::mma_chain(st.tmem + tc::kColP, AB, B3, 128, 64, 64, false);
+    if (tid == 0) tc::mma_chain(st.tmem + tc::kColP, AB, B3, 128, 64, 64, false, S::sbo3 * 4);
     if (!tc_issue_wait(st)) return 0.f;
     {
       // A4 (8 tiles of 128 rows): row (xo, y1o, y2o), k = d2; this thread holds y2o = 4*half .. +3
@@ -290,9 +306,9 @@ static __device__ float pair_step_tc(PairTc& st, bool right, const float* Ein, f
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         const int m = row * D + half * 4 + j;
-        float* tile = AB + (m >> 7) * 1024;
-        st4(tile + tc::kmaj(m & 127, 0, 8), v[j * 8 + 0], v[j * 8 + 1], v[j * 8 + 2], v[j * 8 + 3]);
-        st4(tile + tc::kmaj(m & 127, 4, 8), v[j * 8 + 4], v[j * 8 + 5], v[j * 8 + 6], v[j * 8 + 7]);
+        float* tile = AB + (m >> 7) * S::tile4;
+        st4(tile + tc::kmaj_sbo(m & 127, 0, S::sbo4), v[j * 8 + 0], v[j * 8 + 1], v[j * 8 + 2], v[j * 8 + 3]);
+        st4(tile + tc::kmaj_sbo(m & 127, 4, S::sbo4), v[j * 8 + 4], v[j * 8 + 5], v[j * 8 + 6], v[j * 8 + 7]);
       }
     }
     tc::fence_async_smem();
@@ -301,7 +317,8 @@ static __device__ float pair_step_tc(PairTc& st, bool right, const float* Ein, f
     tc::tc_fence_after();
     // ---- s4: eight M=128 tiles accumulate into D4 across the slices
     if (tid == 0)
-      for (int t = 0; t < 8; ++t) tc::mma_chain(st.tmem + tc::kColE + t * 16, AB + t * 1024, B4, 128, 16, 8, s > 0);
+      for (int t = 0; t < 8; ++t)
+        tc::mma_chain(st.tmem + tc::kColE + t * 16, AB + t * S::tile4, B4, 128, 16, 8, s > 0, S::sbo4 * 4);
     if (!tc_issue_wait(st)) return 0.f;
   }
   // ---- result: tile t rows t*128 + row, 16 columns x'o
