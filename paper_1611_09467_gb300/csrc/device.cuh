@@ -553,8 +553,9 @@ __device__ __forceinline__ void householder_fast(float alpha, float ss, float& t
   }
 }
 
-// Division inside the Sturm counts: IEEE in FP64, the hardware approximation
-// (2 ulp) in FP32, where it sits on a long dependent chain.
+// Division inside the Sturm counts and the inverse-iteration factorisation:
+// IEEE in FP64, the hardware approximation (2 ulp) in FP32, where it sits on
+// a long dependent chain.
 __device__ __forceinline__ double sturm_div(double a, double b) { return a / b; }
 __device__ __forceinline__ float sturm_div(float a, float b) { return __fdividef(a, b); }
 
@@ -618,14 +619,14 @@ __device__ void inverse_iteration(const R* t, int n2, R lam, R pivtiny, R* wsR, 
     R d_i, u_i, l;
     if (fabs(cur_d) >= fabs(sub)) {
       d_i = cur_d == R(0) ? pivtiny : cur_d;
-      l = sub / d_i;
+      l = sturm_div(sub, d_i);
       u_i = cur_u;
       next_d -= l * cur_u;
       piv[IX(i)] = 0;
       b[IX(i)] = bi;
       bi = bn - l * bi;
     } else {
-      l = cur_d / sub;
+      l = sturm_div(cur_d, sub);
       d_i = sub;
       u_i = next_d;
       next_d = cur_u - l * next_d;
@@ -635,14 +636,14 @@ __device__ void inverse_iteration(const R* t, int n2, R lam, R pivtiny, R* wsR, 
       bi = bi - l * bn;
     }
     if (fabs(d_i) < pivtiny) d_i = d_i < R(0) ? -pivtiny : pivtiny;
-    rdd[IX(i)] = R(1) / d_i;
+    rdd[IX(i)] = sturm_div(R(1), d_i);
     du[IX(i)] = u_i;
     mult[IX(i)] = l;
     cur_d = next_d;
     cur_u = next_u;
   }
   if (fabs(cur_d) < pivtiny) cur_d = cur_d < R(0) ? -pivtiny : pivtiny;
-  rdd[IX(n2 - 1)] = R(1) / cur_d;
+  rdd[IX(n2 - 1)] = sturm_div(R(1), cur_d);
   du[IX(n2 - 1)] = R(0);
   piv[IX(n2 - 1)] = 0;
   b[IX(n2 - 1)] = bi;
@@ -689,28 +690,34 @@ __device__ __forceinline__ float sel8(const float (&v)[8], int k) {
   for (int q = 1; q < 8; ++q) x = k == q ? v[q] : x;
   return x;
 }
-// column c (run-time index) of a pair-packed 8 x 8 tile
+// Column c of a pair-packed 8 x 8 tile.  c is uniform across the CTA, so a
+// branch on it costs no divergence and each case is eight register moves
+// (selecting by comparisons would cost about seven instructions per entry).
 __device__ __forceinline__ void col_of(const float2 (&a)[8][4], int c, float (&out)[8]) {
-  const int q = c >> 1;
-  const bool hi = c & 1;
-#pragma unroll
-  for (int r = 0; r < 8; ++r) {
-    float2 p = a[r][0];
-#pragma unroll
-    for (int k = 1; k < 4; ++k) p = q == k ? a[r][k] : p;
-    out[r] = hi ? p.y : p.x;
+#define PEPS_COL_CASE(C)                                                      \
+  case C:                                                                     \
+    _Pragma("unroll") for (int r = 0; r < 8; ++r) out[r] = ((C) & 1) ? a[r][(C) >> 1].y : a[r][(C) >> 1].x; \
+    break;
+  switch (c) {
+    PEPS_COL_CASE(0) PEPS_COL_CASE(1) PEPS_COL_CASE(2) PEPS_COL_CASE(3)
+    PEPS_COL_CASE(4) PEPS_COL_CASE(5) PEPS_COL_CASE(6) default: PEPS_COL_CASE(7)
   }
+#undef PEPS_COL_CASE
 }
-// row r (run-time index) of a pair-packed 8 x 8 tile
+// Row r of a pair-packed 8 x 8 tile; r is uniform across the CTA.
 __device__ __forceinline__ void row_of(const float2 (&a)[8][4], int r, float (&out)[8]) {
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    float2 p = a[0][k];
-#pragma unroll
-    for (int rr = 1; rr < 8; ++rr) p = r == rr ? a[rr][k] : p;
-    out[2 * k] = p.x;
-    out[2 * k + 1] = p.y;
+#define PEPS_ROW_CASE(R)                                                      \
+  case R:                                                                     \
+    _Pragma("unroll") for (int k = 0; k < 4; ++k) {                           \
+      out[2 * k] = a[R][k].x;                                                 \
+      out[2 * k + 1] = a[R][k].y;                                             \
+    }                                                                         \
+    break;
+  switch (r) {
+    PEPS_ROW_CASE(0) PEPS_ROW_CASE(1) PEPS_ROW_CASE(2) PEPS_ROW_CASE(3)
+    PEPS_ROW_CASE(4) PEPS_ROW_CASE(5) PEPS_ROW_CASE(6) default: PEPS_ROW_CASE(7)
   }
+#undef PEPS_ROW_CASE
 }
 // Householder bidiagonalisation of an FP32 matrix of at most 128 x 128 held
 // in registers: thread (ti, tj) owns the 8 x 8 tile of rows 8 ti.., columns
@@ -723,9 +730,12 @@ __device__ __forceinline__ void row_of(const float2 (&a)[8][4], int r, float (&o
 // allocation holds the 64-element tile without spilling.  The
 // arithmetic is that of the shared-memory version below (same reflectors,
 // same stored factors); only the order of the partial sums differs.  One
-// column costs three barriers: broadcast of the left reflector, the row norm
-// of the right reflector, and the cross-warp sums of W u.  Warps whose two
-// tile columns lie left of the active column skip the products.  On return W
+// column costs four barriers: broadcast of the left reflector, the row norm
+// of the right reflector, and two for the cross-warp sums of W u (per-warp
+// shares, then row totals).  Column sums within a half-warp are a
+// reduce-scatter followed by an all-gather, the same additions as a
+// butterfly in fewer shuffles.  Warps whose two tile columns lie left of the
+// active column skip the products.  On return W
 // (P x Q, leading dimension ld) holds the unscaled reflectors; t and tau4
 // (tau left, tau right, scale left, scale right, qm apart) are set as by the
 // shared-memory version.
@@ -733,6 +743,7 @@ static __device__ __noinline__ void bidiag_tiles_f32(const float* X, int n, bool
                                                  float* t, float* tau4, int qm) {
   __shared__ __align__(16) float zp[kWarps * 128];   // per-warp partial sums of W u
   __shared__ __align__(16) float vL[128];            // left reflector, by row
+  __shared__ __align__(16) float zt[128];            // row totals of W u
   __shared__ float sc[2 + 16];                       // tau_left, alpha_right, row-norm partials
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, ti = lane & 15;
   const int tj = warp * 2 + (lane >> 4);
@@ -798,13 +809,40 @@ static __device__ __noinline__ void bidiag_tiles_f32(const float* X, int n, bool
             for (int r = 0; r < 8; ++r) s = __ffma2_rn(make_float2(v[r], v[r]), a[r][q], s);
             wc[q] = s;
           }
-#pragma unroll
-          for (int o = 8; o >= 1; o >>= 1)
+          {
+            // reduce-scatter over the half-warp (lane bits 3, 2, 1 pick the
+            // column), then all-gather
+            float w8[8];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-              wc[q].x += __shfl_xor_sync(0xffffffffu, wc[q].x, o);
-              wc[q].y += __shfl_xor_sync(0xffffffffu, wc[q].y, o);
+              w8[2 * q] = wc[q].x;
+              w8[2 * q + 1] = wc[q].y;
             }
+            const bool b3 = lane & 8, b2 = lane & 4, b1 = lane & 2;
+            float k4[4], k2[2];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+              const float snd = b3 ? w8[i] : w8[i + 4], kp = b3 ? w8[i + 4] : w8[i];
+              k4[i] = kp + __shfl_xor_sync(0xffffffffu, snd, 8);
+            }
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+              const float snd = b2 ? k4[i] : k4[i + 2], kp = b2 ? k4[i + 2] : k4[i];
+              k2[i] = kp + __shfl_xor_sync(0xffffffffu, snd, 4);
+            }
+            float k1;
+            {
+              const float snd = b1 ? k2[0] : k2[1], kp = b1 ? k2[1] : k2[0];
+              k1 = kp + __shfl_xor_sync(0xffffffffu, snd, 2);
+            }
+            k1 += __shfl_xor_sync(0xffffffffu, k1, 1);
+            const int hb = lane & 16;
+#pragma unroll
+            for (int c = 0; c < 8; ++c)
+              w8[c] = __shfl_sync(0xffffffffu, k1, hb | ((c >> 2) << 3) | (((c >> 1) & 1) << 2) | ((c & 1) << 1));
+#pragma unroll
+            for (int q = 0; q < 4; ++q) wc[q] = make_float2(w8[2 * q], w8[2 * q + 1]);
+          }
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
             wc[q].x = (c0 + 2 * q > j) ? -tau * wc[q].x : 0.f;
@@ -872,17 +910,24 @@ static __device__ __noinline__ void bidiag_tiles_f32(const float* X, int n, bool
             }
           }
           __syncthreads();
+          // Row totals of W u, one thread per row, the warps' shares added in
+          // warp order; a warp whose columns all lie left of j has a zero
+          // share and did not write it.  Every thread then reads the totals
+          // of its eight rows (one more barrier instead of each of the 16
+          // threads of a row adding all eight shares again).
+          if (tid < 128) {
+            float zs = 0.f;
+#pragma unroll
+            for (int q = 0; q < kWarps; ++q)
+              if (q * 16 + 15 > j) zs += zp[q * 128 + tid];
+            zt[tid] = zs;
+          }
+          __syncthreads();
           if (act) {
-#pragma unroll
-            for (int r = 0; r < 8; ++r) z[r] = 0.f;
-#pragma unroll
-            for (int q = 0; q < kWarps; ++q) {
-              if (q * 16 + 15 <= j) continue;   // that warp's share is zero and was not written
-              const float4 p0 = *reinterpret_cast<const float4*>(zp + q * 128 + r0);
-              const float4 p1 = *reinterpret_cast<const float4*>(zp + q * 128 + r0 + 4);
-              z[0] += p0.x; z[1] += p0.y; z[2] += p0.z; z[3] += p0.w;
-              z[4] += p1.x; z[5] += p1.y; z[6] += p1.z; z[7] += p1.w;
-            }
+            const float4 p0 = *reinterpret_cast<const float4*>(zt + r0);
+            const float4 p1 = *reinterpret_cast<const float4*>(zt + r0 + 4);
+            z[0] = p0.x; z[1] = p0.y; z[2] = p0.z; z[3] = p0.w;
+            z[4] = p1.x; z[5] = p1.y; z[6] = p1.z; z[7] = p1.w;
 #pragma unroll
             for (int r = 0; r < 8; ++r) {
               const float zr = (r0 + r > j) ? -tr * z[r] : 0.f;
