@@ -175,7 +175,7 @@ def run_ours(args, rank, world, local_rank):
 
     build.build()
     torch.cuda.set_device(local_rank)
-    from paper_1611_09467_gb300.peps import measure_peaks
+    from paper_1611_09467_gb300.peps import measure_mma_shape, measure_peaks
     peaks = measure_peaks()
     w = inputs.WORKLOADS[args.workload]
     L, D, Dc, J2 = w["L"], w["D"], w["Dc"], w["J2"]
@@ -279,6 +279,9 @@ def run_ours(args, rank, world, local_rank):
     top = max(kern, key=lambda k: kern[k][0])
     sample = spins[: min(256, n)]
     tc = args.prec == "mixed_tf32" and (D, Dc) == (8, 16)
+    # the tensor-core two-row step issues M128 N64 K8 (s1-s3) and M128 N16 K8
+    # (s4) instructions; their measured rates bound it below the N256 peak
+    mma_rates = {"N64": measure_mma_shape(64), "N16": measure_mma_shape(16)} if tc else None
     fp = "float" if args.prec != "fp64" else "double"
 
     def roof(kname):
@@ -299,10 +302,17 @@ def run_ours(args, rank, world, local_rank):
         else:
             peak, bound, src = peaks["fp32_simt"], "alu", "measured: FP32 FMA on the SIMT pipe (peps_measure_peaks)"
         bpc = DRAM_BYTES_PER_CONFIG.get((args.workload, fp, kname))
-        return {"bound": bound, "kernel": kname, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": bpc * n * args.steps / launches_k if bpc else None,
-                "traffic_unit": "bytes per launch (DRAM read + write, ncu)", "peak_source": src,
-                "flops_per_config": f_cfg, "launches": launches_k}
+        out = {"bound": bound, "kernel": kname, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+               "frac": achieved / peak, "traffic": bpc * n * args.steps / launches_k if bpc else None,
+               "traffic_unit": "bytes per launch (DRAM read + write, ncu)", "peak_source": src,
+               "flops_per_config": f_cfg, "launches": launches_k}
+        if kname == "pair_sandwich" and tc and mma_rates:
+            # per slice: s1 + s2 + s3 at the N64 rate, s4 at the N16 rate
+            f64_, f16_ = 2.0 * 128 * 64 * (16 + 64 + 64), 2.0 * 128 * 16 * 8 * 8
+            ceil_ = (f64_ + f16_) / (f64_ / mma_rates["N64"] + f16_ / mma_rates["N16"])
+            out.update({"mma_shape_rates_tflops": mma_rates, "shape_ceiling_tflops": ceil_,
+                        "frac_of_shape_ceiling": achieved / ceil_})
+        return out
 
     roofline = roof(top)
     other_roofs = {k: roof(k) for k in kern if k != top and roof(k) is not None}

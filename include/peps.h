@@ -408,6 +408,13 @@ peps_status peps_server_stats(peps_server* server, double* stats);
  * the device.  PEPS_ETIMEOUT if the tensor-core probe's bounded wait gave up.
  * The paper has no counterpart. */
 peps_status peps_measure_peaks(double* out /* [3] */);
+/* Measured rate of dense TF32 tcgen05.mma instructions of one shape, M = 128,
+ * N = n (16, 32, 64, 128 or 256), K = 8, both operands in shared memory,
+ * chained into one TMEM accumulator on every SM: *tflops in TFLOP/s.  The
+ * tensor-core kernels issue N = 64 and N = 16 instructions, whose rate can be
+ * below the N = 256 figure of peps_measure_peaks.  Synchronises the device;
+ * PEPS_EINVAL for another n, PEPS_ETIMEOUT if the bounded wait gave up. */
+peps_status peps_measure_tf32_mma_shape(int n, double* tflops);
 
 /* Waits for the context's stream. */
 peps_status peps_synchronize(peps_ctx* ctx);

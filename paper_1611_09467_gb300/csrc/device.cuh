@@ -8,8 +8,26 @@
 
 #include "contract.cuh"
 
-// Phase markers inside the truncation; empty unless a timing harness defines them.
-#ifndef PEPS_PHASE
+// Phase markers inside the truncation.  Empty in the library; the
+// diagnostic build (-DPEPS_PHASE_TIMING, phase_timing.py) makes thread 0 of
+// each CTA add the clock64 cycles since the previous marker to counter k
+// (k = 0: the cycles since the last truncation ended, to counter 7).  Each
+// marker is a barrier there, so that build is only for the breakdown.
+#ifdef PEPS_PHASE_TIMING
+static __device__ unsigned long long peps_phase_cyc[16];
+__device__ __forceinline__ void peps_phase_mark(int k) {
+  __shared__ long long peps_phase_last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const long long t = clock64();
+    const long long d = t - peps_phase_last;
+    if (d > 0 && d < (1ll << 34)) atomicAdd(&peps_phase_cyc[k == 0 ? 7 : k], (unsigned long long)d);
+    peps_phase_last = t;
+  }
+  __syncthreads();
+}
+#define PEPS_PHASE(k) peps_phase_mark(k)
+#else
 #define PEPS_PHASE(k)
 #endif
 
@@ -1357,9 +1375,52 @@ __device__ void cta_topk_left(const R* X, int m, int n, int K, TruncWork<R>& w, 
       }
     }
     const int nref = tall ? Q : Q - 1;
+    bool applied = false;
+    if constexpr (sizeof(R) == 4) {
+      if (tiled && w.wm_shared && Q <= 128 && rowsU <= 128 && K <= 2 * kWarps) {
+        // Reflectors in shared memory, at most 128 rows and 16 columns: one
+        // column of U per half-warp (lane l holds rows l, l + 16, ...), the
+        // reflectors applied one at a time, last first.  Each is a dot
+        // product over the half-warp (shuffles) and an axpy; columns are
+        // independent, so there is no barrier.
+        const int c = warp * 2 + (lane >> 4), l = lane & 15;
+        float u[8];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+          const int i = l + 16 * r;
+          u[r] = (c < K && i < rowsU) ? Uk[i * K + c] : 0.f;
+        }
+        for (int j = nref - 1; j >= 0; --j) {
+          const int pv = tall ? j : j + 1;
+          const float tj = taus[j], sj = scs[j];
+          float v[8], d = 0.f;
+#pragma unroll
+          for (int r = 0; r < 8; ++r) {
+            const int i = l + 16 * r;
+            const float wv = (i > pv && i < rowsU) ? (tall ? W[i * ld + j] : W[j * ld + i]) : 0.f;
+            v[r] = i == pv ? 1.f : sj * wv;
+            d = fmaf(v[r], u[r], d);
+          }
+#pragma unroll
+          for (int o = 8; o >= 1; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+          const float cf = -tj * d;
+#pragma unroll
+          for (int r = 0; r < 8; ++r) u[r] = fmaf(cf, v[r], u[r]);
+        }
+        if (c < K) {
+#pragma unroll
+          for (int r = 0; r < 8; ++r) {
+            const int i = l + 16 * r;
+            if (i < rowsU) Uk[i * K + c] = u[r];
+          }
+        }
+        __syncthreads();
+        applied = true;
+      }
+    }
     const int NB = K < NBMAX ? K : NBMAX;
     R* Vs = Ub;   // [rowsU][nb]
-    for (int j0 = nref > 0 ? ((nref - 1) / NB) * NB : -1; j0 >= 0; j0 -= NB) {
+    for (int j0 = (nref > 0 && !applied) ? ((nref - 1) / NB) * NB : -1; j0 >= 0; j0 -= NB) {
       const int nb = min(NB, nref - j0);
       const int p0 = tall ? j0 : j0 + 1;
       for (int e = tid; e < (rowsU - p0) * nb; e += blockDim.x) {

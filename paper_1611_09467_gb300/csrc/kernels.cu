@@ -781,3 +781,17 @@ extern "C" peps_status peps_amplitudes_static(const peps_params* p, const void* 
   if (r != PEPS_OK) peps::set_last_error(err);
   return r;
 }
+
+#ifdef PEPS_PHASE_TIMING
+// Diagnostic build only: copies the truncation's phase counters (cycles
+// summed over CTAs, see PEPS_PHASE) to out[16] and optionally clears them.
+extern "C" int peps_phase_read(unsigned long long* out, int reset) {
+  if (cudaDeviceSynchronize() != cudaSuccess) return 1;
+  if (cudaMemcpyFromSymbol(out, ::peps_phase_cyc, 16 * sizeof(unsigned long long)) != cudaSuccess) return 1;
+  if (reset) {
+    const unsigned long long z[16] = {0};
+    if (cudaMemcpyToSymbol(::peps_phase_cyc, z, sizeof(z)) != cudaSuccess) return 1;
+  }
+  return 0;
+}
+#endif

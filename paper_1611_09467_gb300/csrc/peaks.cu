@@ -33,11 +33,11 @@ __global__ void __launch_bounds__(kT) k_fma(int iters, T a, T b, T* sink) {
 }
 
 // One CTA per SM (its shared-memory request leaves room for one): thread 0
-// issues `iters` chains of tcgen05.mma kind::tf32, M = 128, N = 256, K = 8 per
-// instruction (4 per chain), from shared-memory operands into one TMEM
-// accumulator, then commits them to an mbarrier and waits (bounded) for
+// issues `iters` chains of tcgen05.mma kind::tf32, M = 128, N = n (<= 256),
+// K = 8 per instruction (4 per chain), from shared-memory operands into one
+// TMEM accumulator, then commits them to an mbarrier and waits (bounded) for
 // their completion.  Operand values are irrelevant.
-__global__ void __launch_bounds__(128) k_tf32_mma(int iters, int* timeout_flag) {
+__global__ void __launch_bounds__(128) k_tf32_mma(int iters, int n, int* timeout_flag) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t tmem_holder;
@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(128) k_tf32_mma(int iters, int* timeout_flag) 
   const uint32_t tmem = tmem_holder;
   bool ok = true;
   if (threadIdx.x == 0) {
-    for (int it = 0; it < iters; ++it) tc::mma_chain(tmem, A, B, 128, 256, 32, it > 0);
+    for (int it = 0; it < iters; ++it) tc::mma_chain(tmem, A, B, 128, n, 32, it > 0);
     tc::commit(&mbar);
     ok = tc::wait_phase(&mbar, 0);
     if (!ok) atomicOr(timeout_flag, 1);
@@ -101,6 +101,37 @@ double time_fma(int nsm, double* tflops) {
   return ms;
 }
 
+
+// Times `iters` chains of M128 x N x K32 TF32 MMAs on every SM (one CTA per SM).
+peps_status time_tf32_mma(int nsm, int n, double* tflops) {
+  using namespace peps::probe;
+  int* flag = nullptr;
+  if (cudaMalloc(&flag, sizeof(int)) != cudaSuccess) return PEPS_ENOMEM;
+  cudaMemset(flag, 0, sizeof(int));
+  const size_t smem = 120 * 1024;   // > half of an SM's shared memory: one CTA per SM
+  cudaFuncSetAttribute(k_tf32_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const int iters = 4096;
+  k_tf32_mma<<<nsm, 128, smem>>>(16, n, flag);   // warm-up
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  cudaEventRecord(a);
+  k_tf32_mma<<<nsm, 128, smem>>>(iters, n, flag);
+  cudaEventRecord(b);
+  cudaEventSynchronize(b);
+  float ms = 0;
+  cudaEventElapsedTime(&ms, a, b);
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  int h = 0;
+  cudaMemcpy(&h, flag, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(flag);
+  if (cudaGetLastError() != cudaSuccess) return PEPS_ECUDA;
+  if (h) return PEPS_ETIMEOUT;
+  *tflops = 2.0 * 128 * n * 32 * (double)iters * nsm / (ms * 1e-3) / 1e12;
+  return PEPS_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -116,32 +147,16 @@ peps_status peps_measure_peaks(double* out) {
       cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return PEPS_ECUDA;
   if (time_fma<float>(nsm, &out[0]) < 0 || time_fma<double>(nsm, &out[1]) < 0) return PEPS_ECUDA;
-  using namespace peps::probe;
-  int* flag = nullptr;
-  if (cudaMalloc(&flag, sizeof(int)) != cudaSuccess) return PEPS_ENOMEM;
-  cudaMemset(flag, 0, sizeof(int));
-  const size_t smem = 120 * 1024;   // > half of an SM's shared memory: one CTA per SM
-  cudaFuncSetAttribute(k_tf32_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  const int iters = 4096;
-  k_tf32_mma<<<nsm, 128, smem>>>(16, flag);   // warm-up
-  cudaEvent_t a, b;
-  cudaEventCreate(&a);
-  cudaEventCreate(&b);
-  cudaEventRecord(a);
-  k_tf32_mma<<<nsm, 128, smem>>>(iters, flag);
-  cudaEventRecord(b);
-  cudaEventSynchronize(b);
-  float ms = 0;
-  cudaEventElapsedTime(&ms, a, b);
-  cudaEventDestroy(a);
-  cudaEventDestroy(b);
-  int h = 0;
-  cudaMemcpy(&h, flag, sizeof(int), cudaMemcpyDeviceToHost);
-  cudaFree(flag);
-  if (cudaGetLastError() != cudaSuccess) return PEPS_ECUDA;
-  if (h) return PEPS_ETIMEOUT;
-  out[2] = 2.0 * 128 * 256 * 32 * (double)iters * nsm / (ms * 1e-3) / 1e12;
-  return PEPS_OK;
+  return time_tf32_mma(nsm, 256, &out[2]);
+}
+
+peps_status peps_measure_tf32_mma_shape(int n, double* tflops) {
+  if (!tflops || !(n == 16 || n == 32 || n == 64 || n == 128 || n == 256)) return PEPS_EINVAL;
+  int dev = 0, nsm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return PEPS_ECUDA;
+  return time_tf32_mma(nsm, n, tflops);
 }
 
 }  // extern "C"

@@ -61,6 +61,7 @@ def lib():
         "peps_gradient_sums": [P, P, i, P, i, P, P, P, P],
         "peps_set_graphs": [P, i],
         "peps_measure_peaks": [P],
+        "peps_measure_tf32_mma_shape": [i, P],
         "peps_set_env_cache": [P, i],
         "peps_set_truncation": [P, i],
         "peps_correlations": [P, P, i, P, i, P, P, P],
@@ -152,6 +153,14 @@ def measure_peaks():
     out = np.zeros(3, dtype=np.float64)
     check(lib().peps_measure_peaks(_ptr(out)))
     return dict(fp32_simt=float(out[0]), fp64_simt=float(out[1]), tf32_tcgen05=float(out[2]))
+
+
+def measure_mma_shape(n):
+    """Measured TFLOP/s of dense TF32 tcgen05.mma instructions M = 128, N = n,
+    K = 8 (operands in shared memory) on the current GPU."""
+    out = np.zeros(1, dtype=np.float64)
+    check(lib().peps_measure_tf32_mma_shape(int(n), _ptr(out)))
+    return float(out[0])
 
 
 def amplitudes_static(A_dev, S, Lx, Ly, D, Dc, prec="fp64"):
