@@ -68,6 +68,55 @@ __device__ __forceinline__ void smem_gemm_km(const R* __restrict__ A, const R* _
   }
 }
 
+// Two products C_h[i][j] = sum_k A_h[k][i] B_h[k][j] (h = 0, 1) of one shape
+// (k-major, shared memory), both at once on 2x4 micro-tiles: where one
+// product has too few 4x4 tiles to occupy the CTA (M = D rows), the two
+// together fill it.  Each output is the same left-to-right chain of FMAs
+// over k as in smem_gemm_km.  B rows are read as 16-byte groups: N, the
+// offsets of the B blocks and their rows must be multiples of 4 reals.  The
+// functor gets (h, i, j, value).
+template <typename R, int M, int N, int K, class Store>
+__device__ __forceinline__ void smem_gemm_km_x2(const R* __restrict__ A0, const R* __restrict__ A1,
+                                                const R* __restrict__ B0, const R* __restrict__ B1, Store st) {
+  static_assert(N % 4 == 0, "B rows are read as groups of four");
+  constexpr int TA = 2, TB = 4;
+  constexpr int TMc = (M + TA - 1) / TA, TNc = N / TB, NT = TMc * TNc;
+  for (int t = threadIdx.x; t < 2 * NT; t += kThreads) {
+    const int h = t / NT, tt = t - h * NT;
+    const R* A = h ? A1 : A0;
+    const R* B = h ? B1 : B0;
+    const int i0 = (tt / TNc) * TA, j0 = (tt % TNc) * TB;
+    R acc[TA][TB];
+#pragma unroll
+    for (int a = 0; a < TA; ++a)
+#pragma unroll
+      for (int b = 0; b < TB; ++b) acc[a][b] = R(0);
+#pragma unroll 4
+    for (int k = 0; k < K; ++k) {
+      R av[TA], bv[TB];
+#pragma unroll
+      for (int q = 0; q < TA; ++q) av[q] = (M % TA == 0 || i0 + q < M) ? A[k * M + i0 + q] : R(0);
+      if constexpr (sizeof(R) == 4) {
+        const float4 b4 = *reinterpret_cast<const float4*>(B + k * N + j0);
+        bv[0] = b4.x; bv[1] = b4.y; bv[2] = b4.z; bv[3] = b4.w;
+      } else {
+        const double2 b01 = *reinterpret_cast<const double2*>(B + k * N + j0);
+        const double2 b23 = *reinterpret_cast<const double2*>(B + k * N + j0 + 2);
+        bv[0] = b01.x; bv[1] = b01.y; bv[2] = b23.x; bv[3] = b23.y;
+      }
+#pragma unroll
+      for (int a = 0; a < TA; ++a)
+#pragma unroll
+        for (int b = 0; b < TB; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+    }
+#pragma unroll
+    for (int a = 0; a < TA; ++a)
+#pragma unroll
+      for (int b = 0; b < TB; ++b)
+        if (M % TA == 0 || i0 + a < M) st(h, i0 + a, j0 + b, acc[a][b]);
+  }
+}
+
 // One fused two-row transfer step.  right == false: left step (E_{c-1} -> E_c);
 // right == true: right step (H_{c+1} -> H_c).  Mu, Md: padded [Dc][D][Dc]
 // boundary-MPS tensors of column c; T1, T2: padded [l][r][u][d] site

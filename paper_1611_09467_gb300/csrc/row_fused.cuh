@@ -99,23 +99,18 @@ __device__ R row_step_fused(bool right, const R* Fin, R* __restrict__ Fout, cons
       }
     }
     __syncthreads();
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      R* Pb = Pb0 + h * S::P;
-      smem_gemm_km<R, D, D * Dc, Dc>(Fs0 + (2 * par + h) * S::FS, Mus, [&](int i, int j, R v) {
-        const int u = j / Dc, xo = j % Dc;      // i = yi, j = (u, xo)
-        Pb[(i * D + u) * Dc + xo] = v;
-      });
-    }
+    // the two slices of the pair together: each product alone has too few
+    // 4x4 tiles to occupy the CTA
+    smem_gemm_km_x2<R, D, D * Dc, Dc>(Fs0 + (2 * par) * S::FS, Fs0 + (2 * par + 1) * S::FS, Mus, Mus,
+                                      [&](int h, int i, int j, R v) {
+                                        const int u = j / Dc, xo = j % Dc;      // i = yi, j = (u, xo)
+                                        Pb0[h * S::P + (i * D + u) * Dc + xo] = v;
+                                      });
     __syncthreads();
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      R* Qb = Qb0 + h * S::Q;
-      smem_gemm_km<R, Dc, DD, DD>(Pb0 + h * S::P, Ts, [&](int i, int j, R v) {
-        const int yo = j / D, d = j % D;        // i = xo, j = (yo, d)
-        Qb[d * XY + i * D + yo] = v;
-      });
-    }
+    smem_gemm_km_x2<R, Dc, DD, DD>(Pb0, Pb0 + S::P, Ts, Ts, [&](int h, int i, int j, R v) {
+      const int yo = j / D, d = j % D;          // i = xo, j = (yo, d)
+      Qb0[h * S::Q + d * XY + i * D + yo] = v;
+    });
     __syncthreads();
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
@@ -200,15 +195,12 @@ __device__ void site_env_fused(const R* F, const R* __restrict__ Mu, const R* __
     }
     __syncthreads();
     // X: rows l, cols (u, b), k = a;  Y: rows d, cols (b, r), k = b'
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      R* Xs = Xs0 + h * Dc * DD;
-      R* Ys = Ys0 + h * Dc * DD;
-      smem_gemm_km<R, D, D * Dc, Dc>(Fs0 + h * S::FS, Mus,
-                                     [&](int i, int j, R v) { Xs[(j % Dc) * DD + i * D + j / Dc] = v; });
-      smem_gemm_km<R, D, Dc * D, Dc>(Mdk0 + h * S::MD, Gs,
-                                     [&](int i, int j, R v) { Ys[(j / D) * DD + i * D + j % D] = v; });
-    }
+    smem_gemm_km_x2<R, D, D * Dc, Dc>(Fs0, Fs0 + S::FS, Mus, Mus, [&](int h, int i, int j, R v) {
+      Xs0[h * Dc * DD + (j % Dc) * DD + i * D + j / Dc] = v;
+    });
+    smem_gemm_km_x2<R, D, Dc * D, Dc>(Mdk0, Mdk0 + S::MD, Gs, Gs, [&](int h, int i, int j, R v) {
+      Ys0[h * Dc * DD + (j / D) * DD + i * D + j % D] = v;
+    });
     __syncthreads();
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
