@@ -762,7 +762,8 @@ static __device__ __noinline__ void bidiag_tiles_f32(const float* X, int n, bool
   __shared__ __align__(16) float zp[kWarps * 128];   // per-warp partial sums of W u
   __shared__ __align__(16) float vL[128];            // left reflector, by row
   __shared__ __align__(16) float zt[128];            // row totals of W u
-  __shared__ float sc[2 + 16];                       // tau_left, alpha_right, row-norm partials
+  __shared__ float sc[2];                            // tau_left, alpha_right
+  __shared__ __align__(16) float rnp[16];            // row-norm partials, by tile column
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, ti = lane & 15;
   const int tj = warp * 2 + (lane >> 4);
   const int r0 = ti * 8, c0 = tj * 8;
@@ -889,12 +890,18 @@ static __device__ __noinline__ void bidiag_tiles_f32(const float* X, int n, bool
                 if (c0 + c > j + 1) ss = fmaf(row[c], row[c], ss);
               if (tj == ta) sc[1] = sel8(row, ja);
             }
-            sc[2 + tj] = ss;
+            rnp[tj] = ss;
           }
           __syncthreads();
           float ssr = 0.f;
 #pragma unroll
-          for (int q = 0; q < 16; ++q) ssr += sc[2 + q];
+          for (int q = 0; q < 16; q += 4) {
+            const float4 p4 = *reinterpret_cast<const float4*>(rnp + q);
+            ssr += p4.x;
+            ssr += p4.y;
+            ssr += p4.z;
+            ssr += p4.w;
+          }
           float tr, sr, br;
           householder_fast(sc[1], ssr, tr, sr, br);
           if (tid == 0) {
