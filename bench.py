@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--serve", action="store_true",
                     help="serving benchmark: Poisson stream of requests over mixed lattices (continuous batching)")
     ap.add_argument("--serve-seconds", type=float, default=30.0)
+    ap.add_argument("--serve-policy", choices=("fifo", "expected"), default="fifo",
+                    help="admission order of queued requests in --serve")
     ap.add_argument("--lanes", type=int, default=4)
     ap.add_argument("--autotune", action=argparse.BooleanOptionalAction, default=True,
                     help="pick kernel variants and grids with peps_autotune on a probe batch first")
@@ -444,6 +446,7 @@ def run_serving(args):
     torch.cuda.synchronize()
     srv2 = Server(nlanes=args.lanes, hbm_budget_gb=budget)
     srv2.set_packing(512, 4)
+    srv2.set_policy(args.serve_policy)
     clk_serve = os.path.join(tempfile.gettempdir(), "peps_bench_clocks_serve.csv")
     sampler, fh = start_clock_sampler(clk_serve)
     t0 = time.perf_counter()
@@ -470,6 +473,8 @@ def run_serving(args):
                    "configs_per_request": "uniform 256..1024", "outputs": "ln|psi|, sign, E_loc, Delta",
                    "arrivals": f"Poisson, {rate:.2f}/s (80% of the closed-loop capacity {capacity:.2f}/s)",
                    "packing": "requests of <= 512 configurations, up to 4 models per launch",
+                   "admission": {"fifo": "first come first served",
+                                 "expected": "smallest expected run time less time waited first"}[args.serve_policy],
                    "lanes": args.lanes, "hbm_budget_gb": budget,
                    "duration_s": args.serve_seconds},
         "server": st, "probe_ms_per_model": probe_ms,

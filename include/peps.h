@@ -390,6 +390,14 @@ peps_status peps_server_submit_chain(peps_server* server, peps_ctx* model, uint6
  * their boundary sweeps share one kernel.  max_configs = 0 (the default)
  * turns packing off.  Results equal the requests run alone. */
 peps_status peps_server_set_packing(peps_server* server, int max_configs, int max_requests);
+/* Admission order of queued requests.  0 (the default): first come first
+ * served.  1: smallest expected run time less time waited first, where the
+ * expected run time is the request's configurations times its model's
+ * running average of milliseconds per configuration over finished launches
+ * (0 before the model's first), so short requests pass long ones until the
+ * long ones have waited about as long as they will run.  Results do not
+ * depend on the order.  PEPS_EINVAL for another value. */
+peps_status peps_server_set_policy(peps_server* server, int policy);
 /* Retires finished requests and admits queued ones.  wait != 0 blocks until
  * at least one request finishes (or nothing is left).  Up to max finished ids
  * and their latencies (ms, submission to completion) are written; *ndone is

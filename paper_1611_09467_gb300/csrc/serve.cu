@@ -11,7 +11,11 @@
 // rebuild workspaces; idle workers are freed only when the budget requires.
 // Requests wait in a queue until a lane is free and the HBM they need fits
 // under the budget (footprint admission); a request that does not fit lets
-// smaller queued ones pass.  Completion is
+// smaller queued ones pass.  Queued requests are admitted first come first
+// served, or (peps_server_set_policy) by expected run time less the time
+// they have waited: the expected run time is the request's configurations
+// times its model's milliseconds per configuration, a running average over
+// the model's finished launches.  Completion is
 // observed through one event per lane; the latency of a request runs from
 // submission to the poll that sees its event.  Results do not depend on the
 // lane or on what else runs: every configuration is evaluated by the same
@@ -60,6 +64,8 @@ struct Lane {
   cudaEvent_t done = nullptr;
   bool busy = false;
   std::vector<Request> reqs;   // the request, or the requests packed into one launch
+  Clock::time_point launched;  // when its launch was issued
+  int launched_n = 0;          // configurations in it
   // worker contexts of this lane, one per model, least recently used first
   std::vector<Worker> workers;
   peps_packer* packer = nullptr;
@@ -78,6 +84,8 @@ struct peps_server {
   std::deque<std::pair<long long, double>> finished;   // retired, not yet reported by poll
   size_t peak_bytes = 0;
   int pack_max = 0, pack_width = 1;   // packing of small requests (peps_server_set_packing)
+  int policy = 0;                     // 0 first come first served, 1 by expected run time less wait
+  std::vector<std::pair<const peps_ctx*, double>> cost;   // per model: ms per configuration
 };
 
 namespace {
@@ -167,6 +175,8 @@ peps_status launch(peps_server* s, Lane& l, const Request& r) {
   if (cudaEventRecord(l.done, l.stream) != cudaSuccess) return PEPS_ECUDA;
   l.busy = true;
   l.reqs.assign(1, r);
+  l.launched = Clock::now();
+  l.launched_n = r.n;
   s->peak_bytes = std::max(s->peak_bytes, in_use(s));
   return PEPS_OK;
 }
@@ -205,8 +215,36 @@ peps_status launch_packed(peps_server* s, Lane& l, const std::vector<Request>& r
   if (cudaEventRecord(l.done, l.stream) != cudaSuccess) return PEPS_ECUDA;
   l.busy = true;
   l.reqs = rs;
+  l.launched = Clock::now();
+  l.launched_n = 0;
+  for (const Request& r : rs) l.launched_n += r.n;
   s->peak_bytes = std::max(s->peak_bytes, in_use(s));
   return PEPS_OK;
+}
+
+// Expected run time of a request: its configurations times its model's
+// running average of milliseconds per configuration (0 before the model's
+// first finished launch, so a new model goes first).
+double expected_ms(const peps_server* s, const Request& r) {
+  for (const auto& c : s->cost)
+    if (c.first == r.model) return c.second * r.n;
+  return 0.0;
+}
+
+// Folds a finished launch into its models' averages: milliseconds from issue
+// to the poll that saw it finish, per configuration of the launch.
+void record_cost(peps_server* s, const Lane& l) {
+  if (l.launched_n < 1) return;
+  const double per = std::chrono::duration<double, std::milli>(Clock::now() - l.launched).count() / l.launched_n;
+  for (const Request& r : l.reqs) {
+    bool found = false;
+    for (auto& c : s->cost)
+      if (c.first == r.model) {
+        c.second = 0.5 * c.second + 0.5 * per;
+        found = true;
+      }
+    if (!found) s->cost.emplace_back(r.model, per);
+  }
 }
 
 bool packable(const peps_server* s, const Request& r) {
@@ -221,6 +259,7 @@ peps_status step(peps_server* s) {
     if (q == cudaErrorNotReady) continue;
     if (q != cudaSuccess) return PEPS_ECUDA;
     l.busy = false;
+    record_cost(s, l);
     for (const Request& r : l.reqs) {
       const double ms = std::chrono::duration<double, std::milli>(Clock::now() - r.submitted).count();
       s->completed += 1;
@@ -229,67 +268,87 @@ peps_status step(peps_server* s) {
     }
     l.reqs.clear();
   }
-  for (auto it = s->queue.begin(); it != s->queue.end();) {
-    Lane* free_lane = nullptr;
-    // prefer a free lane whose worker of this model last held these
-    // configurations (its environment cache), then one with a worker of the model
-    auto score = [&](const Lane& l) {
-      const int k = find_worker(l, it->model);
-      if (k < 0) return 0;
-      return l.workers[k].last_S == it->S ? 2 : 1;
-    };
-    for (Lane& l : s->lanes)
-      if (!l.busy && (!free_lane || score(l) > score(*free_lane))) free_lane = &l;
-    if (!free_lane) break;
-    const size_t extra = extra_bytes(s, *free_lane, *it);
-    const int k = find_worker(*free_lane, it->model);
-    if (!make_room(s, extra, k >= 0 ? free_lane->workers[k].ctx : nullptr)) {
-      ++it;   // does not fit now: let a smaller queued request pass
-      continue;
+  for (;;) {
+    bool any_free = false;
+    for (const Lane& l : s->lanes) any_free = any_free || !l.busy;
+    if (!any_free || s->queue.empty()) break;
+    // candidates in admission order
+    std::vector<size_t> order(s->queue.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = i;
+    if (s->policy == 1) {
+      const auto now = Clock::now();
+      std::vector<double> key(order.size());
+      for (size_t i = 0; i < order.size(); ++i)
+        key[i] = expected_ms(s, s->queue[i]) -
+                 std::chrono::duration<double, std::milli>(now - s->queue[i].submitted).count();
+      std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) { return key[x] < key[y]; });
     }
-    // co-admit other small queued requests of distinct models and the same
-    // precision class into one packed launch
-    std::vector<std::deque<Request>::iterator> group;
-    if (packable(s, *it)) {
-      group.push_back(it);
-      size_t grown = extra;
-      for (auto jt = std::next(it); jt != s->queue.end() && (int)group.size() < s->pack_width; ++jt) {
-        if (!packable(s, *jt) || peps::ctx_is_fp64(jt->model) != peps::ctx_is_fp64(it->model)) continue;
-        bool dup = false;
-        for (auto& g : group) dup = dup || g->model == jt->model;
-        if (dup) continue;
-        const size_t e2 = extra_bytes(s, *free_lane, *jt);
-        if (in_use(s) + grown + e2 > s->budget) continue;
-        grown += e2;
-        group.push_back(jt);
+    bool admitted = false;
+    for (size_t oi : order) {
+      auto it = s->queue.begin() + (std::ptrdiff_t)oi;
+      Lane* free_lane = nullptr;
+      // prefer a free lane whose worker of this model last held these
+      // configurations (its environment cache), then one with a worker of the model
+      auto score = [&](const Lane& l) {
+        const int k = find_worker(l, it->model);
+        if (k < 0) return 0;
+        return l.workers[k].last_S == it->S ? 2 : 1;
+      };
+      for (Lane& l : s->lanes)
+        if (!l.busy && (!free_lane || score(l) > score(*free_lane))) free_lane = &l;
+      const size_t extra = extra_bytes(s, *free_lane, *it);
+      const int k = find_worker(*free_lane, it->model);
+      if (!make_room(s, extra, k >= 0 ? free_lane->workers[k].ctx : nullptr))
+        continue;   // does not fit now: let a smaller queued request pass
+      // co-admit other small queued requests of distinct models and the same
+      // precision class into one packed launch (first come first served: only
+      // requests behind this one)
+      std::vector<std::deque<Request>::iterator> group;
+      if (packable(s, *it)) {
+        group.push_back(it);
+        size_t grown = extra;
+        for (auto jt = s->queue.begin(); jt != s->queue.end() && (int)group.size() < s->pack_width; ++jt) {
+          if (jt == it || (s->policy == 0 && jt < it)) continue;
+          if (!packable(s, *jt) || peps::ctx_is_fp64(jt->model) != peps::ctx_is_fp64(it->model)) continue;
+          bool dup = false;
+          for (auto& g : group) dup = dup || g->model == jt->model;
+          if (dup) continue;
+          const size_t e2 = extra_bytes(s, *free_lane, *jt);
+          if (in_use(s) + grown + e2 > s->budget) continue;
+          grown += e2;
+          group.push_back(jt);
+        }
       }
+      peps_status st;
+      if (group.size() > 1) {
+        std::vector<Request> rs;
+        for (auto& g : group) rs.push_back(*g);
+        st = launch_packed(s, *free_lane, rs);
+      } else {
+        st = launch(s, *free_lane, *it);
+        group.assign(1, it);
+      }
+      if (st != PEPS_OK) {
+        // The request cannot run (its workspace does not fit in device memory,
+        // or a launch failed).  It is retired as failed, with a negative
+        // latency, so that the queue keeps moving; peps_last_error holds why.
+        for (auto& g : group) s->finished.emplace_back(g->id, -1.0);
+      }
+      // remove the group from the queue (erasing inside a deque invalidates
+      // its iterators, so the candidates are ordered again; every admission
+      // occupies a lane, so this ends once the lanes are busy or nothing
+      // more fits)
+      std::vector<long long> ids;
+      for (auto& g : group) ids.push_back(g->id);
+      s->queue.erase(std::remove_if(s->queue.begin(), s->queue.end(),
+                                    [&](const Request& q) {
+                                      return std::find(ids.begin(), ids.end(), q.id) != ids.end();
+                                    }),
+                     s->queue.end());
+      admitted = true;
+      break;
     }
-    peps_status st;
-    if (group.size() > 1) {
-      std::vector<Request> rs;
-      for (auto& g : group) rs.push_back(*g);
-      st = launch_packed(s, *free_lane, rs);
-    } else {
-      st = launch(s, *free_lane, *it);
-      group.assign(1, it);
-    }
-    if (st != PEPS_OK) {
-      // The request cannot run (its workspace does not fit in device memory,
-      // or a launch failed).  It is retired as failed, with a negative
-      // latency, so that the queue keeps moving; peps_last_error holds why.
-      for (auto& g : group) s->finished.emplace_back(g->id, -1.0);
-    }
-    // remove the group from the queue (erasing inside a deque invalidates
-    // its iterators, so the scan starts again; every admission occupies a
-    // lane, so this ends once the lanes are busy or nothing more fits)
-    std::vector<long long> ids;
-    for (auto& g : group) ids.push_back(g->id);
-    s->queue.erase(std::remove_if(s->queue.begin(), s->queue.end(),
-                                  [&](const Request& q) {
-                                    return std::find(ids.begin(), ids.end(), q.id) != ids.end();
-                                  }),
-                   s->queue.end());
-    it = s->queue.begin();
+    if (!admitted) break;
   }
   return PEPS_OK;
 }
@@ -383,6 +442,15 @@ peps_status peps_server_set_packing(peps_server* s, int max_configs, int max_req
   }
   s->pack_max = max_configs;
   s->pack_width = max_requests;
+  return PEPS_OK;
+}
+
+peps_status peps_server_set_policy(peps_server* s, int policy) {
+  if (!s || policy < 0 || policy > 1) {
+    peps::set_last_error("policy is 0 (first come first served) or 1 (expected run time less wait)");
+    return PEPS_EINVAL;
+  }
+  s->policy = policy;
   return PEPS_OK;
 }
 

@@ -107,7 +107,7 @@ def exported_symbols():
              "peps_gradient_sums", "peps_gradient_sums_len", "peps_gradient_finalize", "peps_set_graphs",
              "peps_graph_stats", "peps_correlations", "peps_set_env_cache", "peps_set_truncation", "peps_measure_peaks",
              "peps_server_create",
-             "peps_server_destroy", "peps_server_submit", "peps_server_submit_chain", "peps_server_set_packing",
+             "peps_server_destroy", "peps_server_submit", "peps_server_submit_chain", "peps_server_set_packing", "peps_server_set_policy",
              "peps_server_poll", "peps_server_stats", "peps_su_create", "peps_su_destroy", "peps_su_evolve", "peps_su_to_peps",
              "peps_autotune", "peps_tuned_config", "peps_packer_create", "peps_packer_destroy",
              "peps_packer_evaluate"]

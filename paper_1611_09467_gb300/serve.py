@@ -26,8 +26,10 @@ def _lib():
         L.peps_server_submit_chain.argtypes = [P, P, P, i, i, u64, u64, u64, P, P, P, P, P,
                                                ctypes.POINTER(ctypes.c_longlong)]
         L.peps_server_set_packing.argtypes = [P, i, i]
+        L.peps_server_set_policy.argtypes = [P, i]
         for f in ("peps_server_create", "peps_server_destroy", "peps_server_submit", "peps_server_poll",
-                  "peps_server_stats", "peps_server_submit_chain", "peps_server_set_packing"):
+                  "peps_server_stats", "peps_server_submit_chain", "peps_server_set_packing",
+                  "peps_server_set_policy"):
             getattr(L, f).restype = ctypes.c_int
         L._server_sigs = True
     return L
@@ -100,6 +102,12 @@ class Server:
         """Pack co-admitted requests of at most ``max_configs`` configurations
         (up to ``max_requests`` of distinct models) into one launch; 0 turns it off."""
         _p.check(_lib().peps_server_set_packing(self.h, int(max_configs), int(max_requests)))
+
+    def set_policy(self, policy):
+        """Admission order: "fifo" (first come first served, the default) or
+        "expected" (smallest expected run time less time waited first)."""
+        code = {"fifo": 0, "expected": 1}[policy]
+        _p.check(_lib().peps_server_set_policy(self.h, code))
 
     def poll(self, wait=False, max_items=256):
         """[(request id, latency ms)] of requests finished since the last poll."""

@@ -62,12 +62,14 @@ def test_results_alone_equal_results_in_the_mix():
         m.close()
 
 
-def test_mix_with_packing_chains_and_a_tensor_core_model():
+@pytest.mark.parametrize("policy", ["fifo", "expected"])
+def test_mix_with_packing_chains_and_a_tensor_core_model(policy):
     """A mix of a mixed-TF32 tensor-core model (D=8, Dc=16), FP32 and FP64
     models: small requests co-admitted into packed launches, chain requests
     whose resident configurations take Metropolis sweeps on the server, and
-    Delta requested too.  Every result equals the same work run alone
-    (chain requests: the same sweeps and evaluation on a copy)."""
+    Delta requested too, under either admission order.  Every result equals
+    the same work run alone (chain requests: the same sweeps and evaluation
+    on a copy)."""
     from paper_1611_09467_gb300.peps import PEPS
     from paper_1611_09467_gb300.serve import Server
     models = [PEPS(inputs.make_tensors(6, 6, 8, 211), 6, 6, 8, 16, J1=1.0, J2=0.5, prec="mixed_tf32"),
@@ -77,6 +79,7 @@ def test_mix_with_packing_chains_and_a_tensor_core_model():
     rng = np.random.default_rng(215)
     srv = Server(nlanes=2, hbm_budget_gb=4.0)
     srv.set_packing(64, 4)
+    srv.set_policy(policy)
     plain, chains = [], []
     for k in range(10):
         m = models[k % 4]

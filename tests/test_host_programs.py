@@ -198,3 +198,4 @@ def test_server_argument_checks():
     assert "bad request" in L.peps_last_error().decode()
     st = np.zeros(8)
     assert L.peps_server_stats(None, st.ctypes.data) == 1
+    assert L.peps_server_set_policy(None, 1) == 1
