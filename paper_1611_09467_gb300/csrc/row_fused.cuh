@@ -79,7 +79,14 @@ __device__ R row_step_fused(bool right, const R* Fin, R* __restrict__ Fout, cons
     const int a = right ? xout : xin, b = right ? xin : xout;
     Mus[e] = Mu[a * D * Dc + u * Dc + b];
   }
-  // thread t owns outputs o = q * kThreads + t, o = x'o * XY + (xo, yo)
+  // Outputs o = x'o * XY + (xo, yo).  When the CTA splits into whole groups
+  // of XY threads, thread t owns row (xo, yo) = t % XY and the OPT
+  // consecutive x'o from (t / XY) * OPT, so the Q entry of a row is loaded
+  // once per d and the Md entries as 16-byte groups; otherwise t owns
+  // o = q * kThreads + t.
+  constexpr bool grouped = kThreads % XY == 0 && Dc % (kThreads / XY) == 0 && S::OPT == Dc / (kThreads / XY);
+  const int grow = tid % XY, gx = (tid / XY) * S::OPT;
+  auto out_index = [&](int q) { return grouped ? (gx + q) * XY + grow : q * kThreads + tid; };
   R acc[S::OPT];
 #pragma unroll
   for (int q = 0; q < S::OPT; ++q) acc[q] = R(0);
@@ -116,15 +123,36 @@ __device__ R row_step_fused(bool right, const R* Fin, R* __restrict__ Fout, cons
     for (int h = 0; h < 2; ++h) {
       const R* Qb = Qb0 + h * S::Q;
       const R* Mds = Mds0 + (2 * par + h) * S::MD;
+      if constexpr (grouped) {
+        // per output the same chain of FMAs over d as below
 #pragma unroll
-      for (int q = 0; q < S::OPT; ++q) {
-        const int o = q * kThreads + tid;
-        if (S::OUT % kThreads == 0 || o < S::OUT) {
-          const int row = o % XY, xo2 = o / XY;
-          R v = acc[q];
+        for (int d = 0; d < D; ++d) {
+          const R qv = Qb[d * XY + grow];
+          R md[S::OPT];
+          if constexpr (sizeof(R) == 4 && S::OPT % 4 == 0) {
 #pragma unroll
-          for (int d = 0; d < D; ++d) v = fma(Qb[d * XY + row], Mds[d * Dc + xo2], v);
-          acc[q] = v;
+            for (int q = 0; q < S::OPT; q += 4) {
+              const float4 m4 = *reinterpret_cast<const float4*>(Mds + d * Dc + gx + q);
+              md[q] = m4.x; md[q + 1] = m4.y; md[q + 2] = m4.z; md[q + 3] = m4.w;
+            }
+          } else {
+#pragma unroll
+            for (int q = 0; q < S::OPT; ++q) md[q] = Mds[d * Dc + gx + q];
+          }
+#pragma unroll
+          for (int q = 0; q < S::OPT; ++q) acc[q] = fma(qv, md[q], acc[q]);
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < S::OPT; ++q) {
+          const int o = q * kThreads + tid;
+          if (S::OUT % kThreads == 0 || o < S::OUT) {
+            const int row = o % XY, xo2 = o / XY;
+            R v = acc[q];
+#pragma unroll
+            for (int d = 0; d < D; ++d) v = fma(Qb[d * XY + row], Mds[d * Dc + xo2], v);
+            acc[q] = v;
+          }
         }
       }
     }
@@ -134,21 +162,21 @@ __device__ R row_step_fused(bool right, const R* Fin, R* __restrict__ Fout, cons
     R mx = R(0);
 #pragma unroll
     for (int q = 0; q < S::OPT; ++q)
-      if (S::OUT % kThreads == 0 || q * kThreads + tid < S::OUT) mx = fmax(mx, fabs(acc[q]));
+      if (grouped || S::OUT % kThreads == 0 || q * kThreads + tid < S::OUT) mx = fmax(mx, fabs(acc[q]));
     const int e = pow2_exponent(block_max(mx, red));
     const R sc = pow2<R>(-e);
     if (e_out) *e_out = e;
 #pragma unroll
     for (int q = 0; q < S::OPT; ++q) {
-      const int o = q * kThreads + tid;
-      if (S::OUT % kThreads == 0 || o < S::OUT) Fout[o] = acc[q] * sc;
+      const int o = out_index(q);
+      if (grouped || S::OUT % kThreads == 0 || o < S::OUT) Fout[o] = acc[q] * sc;
     }
     __syncthreads();
   } else {
 #pragma unroll
     for (int q = 0; q < S::OPT; ++q) {
-      const int o = q * kThreads + tid;
-      if (S::OUT % kThreads == 0 || o < S::OUT) dot = fma(acc[q], Gdot[o], dot);
+      const int o = out_index(q);
+      if (grouped || S::OUT % kThreads == 0 || o < S::OUT) dot = fma(acc[q], Gdot[o], dot);
     }
     dot = block_sum(dot, red);
   }
