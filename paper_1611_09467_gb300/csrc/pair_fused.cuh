@@ -35,6 +35,19 @@ struct PairSmem {
   static constexpr int RPT = (ROWS + kThreads - 1) / kThreads;   // rows per thread
 };
 
+// Four consecutive reals from a 16-byte aligned shared-memory address.
+template <typename R>
+__device__ __forceinline__ void load4(const R* p, R (&v)[4]) {
+  if constexpr (sizeof(R) == 4) {
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+  } else {
+    const double2 a = *reinterpret_cast<const double2*>(p);
+    const double2 b = *reinterpret_cast<const double2*>(p + 2);
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+  }
+}
+
 // C[i][j] for a k-major pair A[K][M], B[K][N] in shared memory; the caller's
 // functor places each output.  Every thread handles 4x4 micro-tiles.
 template <typename R, int M, int N, int K, class Store>
@@ -50,10 +63,16 @@ __device__ __forceinline__ void smem_gemm_km(const R* __restrict__ A, const R* _
 #pragma unroll 4
     for (int k = 0; k < K; ++k) {
       R av[4], bv[4];
+      if constexpr (M % 4 == 0 && N % 4 == 0) {
+        // 16-byte groups (the callers' blocks start at multiples of 4 reals)
+        load4(A + k * M + i0, av);
+        load4(B + k * N + j0, bv);
+      } else {
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        av[q] = (M % 4 == 0 || i0 + q < M) ? A[k * M + i0 + q] : R(0);
-        bv[q] = (N % 4 == 0 || j0 + q < N) ? B[k * N + j0 + q] : R(0);
+        for (int q = 0; q < 4; ++q) {
+          av[q] = (M % 4 == 0 || i0 + q < M) ? A[k * M + i0 + q] : R(0);
+          bv[q] = (N % 4 == 0 || j0 + q < N) ? B[k * N + j0 + q] : R(0);
+        }
       }
 #pragma unroll
       for (int a = 0; a < 4; ++a)
@@ -96,14 +115,7 @@ __device__ __forceinline__ void smem_gemm_km_x2(const R* __restrict__ A0, const 
       R av[TA], bv[TB];
 #pragma unroll
       for (int q = 0; q < TA; ++q) av[q] = (M % TA == 0 || i0 + q < M) ? A[k * M + i0 + q] : R(0);
-      if constexpr (sizeof(R) == 4) {
-        const float4 b4 = *reinterpret_cast<const float4*>(B + k * N + j0);
-        bv[0] = b4.x; bv[1] = b4.y; bv[2] = b4.z; bv[3] = b4.w;
-      } else {
-        const double2 b01 = *reinterpret_cast<const double2*>(B + k * N + j0);
-        const double2 b23 = *reinterpret_cast<const double2*>(B + k * N + j0 + 2);
-        bv[0] = b01.x; bv[1] = b01.y; bv[2] = b23.x; bv[3] = b23.y;
-      }
+      load4(B + k * N + j0, bv);
 #pragma unroll
       for (int a = 0; a < TA; ++a)
 #pragma unroll

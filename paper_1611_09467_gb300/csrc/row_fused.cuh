@@ -242,10 +242,15 @@ __device__ void site_env_fused(const R* F, const R* __restrict__ Mu, const R* __
 #pragma unroll 4
           for (int b = 0; b < Dc; ++b) {
             R xv[4], yv[4];
+            if constexpr (DD % 4 == 0) {
+              load4(Xs + b * DD + i0, xv);
+              load4(Ys + b * DD + j0, yv);
+            } else {
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              xv[q] = (DD % 4 == 0 || i0 + q < DD) ? Xs[b * DD + i0 + q] : R(0);
-              yv[q] = (DD % 4 == 0 || j0 + q < DD) ? Ys[b * DD + j0 + q] : R(0);
+              for (int q = 0; q < 4; ++q) {
+                xv[q] = (DD % 4 == 0 || i0 + q < DD) ? Xs[b * DD + i0 + q] : R(0);
+                yv[q] = (DD % 4 == 0 || j0 + q < DD) ? Ys[b * DD + j0 + q] : R(0);
+              }
             }
 #pragma unroll
             for (int i = 0; i < 4; ++i)
