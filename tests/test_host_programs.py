@@ -28,6 +28,18 @@ def test_exports_every_declared_symbol():
     assert peps.lib().peps_status_str(5) == b"PEPS_ENUMERIC"
 
 
+def test_phase_timing_build_exports_its_counters():
+    """The diagnostic build behind phase_timing.py compiles (every source with
+    -DPEPS_PHASE_TIMING, into its own directory) and exports the counter
+    reader; the library itself does not have it."""
+    import ctypes
+    path = build.build(phase_timing=True)
+    assert path != build.LIB and os.path.exists(path)
+    D = ctypes.CDLL(path)
+    assert hasattr(D, "peps_phase_read") and hasattr(D, "peps_create")
+    assert not hasattr(peps.lib(), "peps_phase_read")
+
+
 def _pad(t, shape):
     out = np.zeros(shape)
     out[tuple(slice(0, s) for s in t.shape)] = t
