@@ -88,17 +88,20 @@ __device__ __forceinline__ void smem_gemm_km(const R* __restrict__ A, const R* _
 }
 
 // Two products C_h[i][j] = sum_k A_h[k][i] B_h[k][j] (h = 0, 1) of one shape
-// (k-major, shared memory), both at once on 2x4 micro-tiles: where one
+// (k-major, shared memory), both at once on TA x 4 micro-tiles: where one
 // product has too few 4x4 tiles to occupy the CTA (M = D rows), the two
-// together fill it.  Each output is the same left-to-right chain of FMAs
-// over k as in smem_gemm_km.  B rows are read as 16-byte groups: N, the
-// offsets of the B blocks and their rows must be multiples of 4 reals.  The
-// functor gets (h, i, j, value).
-template <typename R, int M, int N, int K, class Store>
+// together fill it with TA = 2; with a long reduction TA = 4 halves the
+// shared-memory reads per multiply-add.  Each output is the same
+// left-to-right chain of FMAs over k as in smem_gemm_km.  B rows (and A rows
+// when TA = 4) are read as 16-byte groups: N (M), the offsets of the blocks
+// and their rows must be multiples of 4 reals.  The functor gets (h, i, j,
+// value).
+template <typename R, int M, int N, int K, class Store, int TA = 2>
 __device__ __forceinline__ void smem_gemm_km_x2(const R* __restrict__ A0, const R* __restrict__ A1,
                                                 const R* __restrict__ B0, const R* __restrict__ B1, Store st) {
   static_assert(N % 4 == 0, "B rows are read as groups of four");
-  constexpr int TA = 2, TB = 4;
+  static_assert(TA == 2 || (TA == 4 && M % 4 == 0), "A rows are read as groups of four");
+  constexpr int TB = 4;
   constexpr int TMc = (M + TA - 1) / TA, TNc = N / TB, NT = TMc * TNc;
   for (int t = threadIdx.x; t < 2 * NT; t += kThreads) {
     const int h = t / NT, tt = t - h * NT;
@@ -113,8 +116,12 @@ __device__ __forceinline__ void smem_gemm_km_x2(const R* __restrict__ A0, const 
 #pragma unroll 4
     for (int k = 0; k < K; ++k) {
       R av[TA], bv[TB];
+      if constexpr (TA == 4) {
+        load4(A + k * M + i0, av);
+      } else {
 #pragma unroll
-      for (int q = 0; q < TA; ++q) av[q] = (M % TA == 0 || i0 + q < M) ? A[k * M + i0 + q] : R(0);
+        for (int q = 0; q < TA; ++q) av[q] = (M % TA == 0 || i0 + q < M) ? A[k * M + i0 + q] : R(0);
+      }
       load4(B + k * N + j0, bv);
 #pragma unroll
       for (int a = 0; a < TA; ++a)

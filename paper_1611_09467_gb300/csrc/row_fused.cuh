@@ -114,10 +114,12 @@ __device__ R row_step_fused(bool right, const R* Fin, R* __restrict__ Fout, cons
                                         Pb0[h * S::P + (i * D + u) * Dc + xo] = v;
                                       });
     __syncthreads();
-    smem_gemm_km_x2<R, Dc, DD, DD>(Pb0, Pb0 + S::P, Ts, Ts, [&](int h, int i, int j, R v) {
+    auto store_q = [&](int h, int i, int j, R v) {
       const int yo = j / D, d = j % D;          // i = xo, j = (yo, d)
       Qb0[h * S::Q + d * XY + i * D + yo] = v;
-    });
+    };
+    // K = D^2 is long enough for 4x4 tiles when the rows split into fours
+    smem_gemm_km_x2<R, Dc, DD, DD, decltype(store_q), Dc % 4 == 0 ? 4 : 2>(Pb0, Pb0 + S::P, Ts, Ts, store_q);
     __syncthreads();
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
